@@ -1,0 +1,270 @@
+/*
+ * Shouji CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct restatement of the Shouji pre-alignment
+ * filter (Alser et al., "Shouji: a fast and efficient pre-alignment filter for
+ * sequence alignment", arXiv 1809.07858), one pair at a time, on unpacked
+ * ASCII bytes, with one plain loop per definition.  It exists to check the
+ * CUDA path; only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg may load it.  It shares no code, header, table or layout with the CUDA
+ * library, and it includes nothing from it.
+ *
+ * Notation follows the paper: P is the pattern (the read), T is the text (the
+ * reference segment), both of length m; E is the edit distance threshold.
+ * Indices are 0-based here (the paper is 1-based).
+ *
+ * Readings taken where the paper is silent, ambiguous or garbled (each one is
+ * listed, with its evidence, in the design notes of the repository):
+ *   R1  Orientation.  Rows of the neighborhood map index P, columns index T
+ *       (Eq. 1).  Diagonal d holds, at column c, the comparison of P[c-d]
+ *       with T[c]; d > 0 are the "upper" diagonals (P shifted right, Sec. 2.3)
+ *       and d < 0 the "lower" ones, as printed in Fig. 6.
+ *   R2  Window alignment.  Every 4-bit diagonal segment of search window c
+ *       covers the same four columns c..c+3 (Sec. 2.2.2: "a search window of
+ *       4 columns"; Sec. 2.3: every diagonal is a shifted copy of P compared
+ *       with T at the same positions).
+ *   R3  Cells outside the band (P index c-d outside [0,m)) are mismatches (1).
+ *   R4  There are m windows (Sec. 2.2.2); columns c >= m read as 1 and are
+ *       never written.
+ *   R5  Per window the selection runs over all 2E+1 segments and restarts
+ *       for every window (Sec. 2.2.2 Step 1), in the order lower_1, upper_1,
+ *       lower_2, upper_2, ..., lower_E, upper_E: a segment replaces the
+ *       current choice when it has more zeros, or the same number of zeros
+ *       while it starts with a zero and the current choice does not ("the
+ *       first one that has a leading zero").  The main diagonal is examined
+ *       last and replaces the choice only with strictly more zeros
+ *       (Algorithm 1, step 2).  With E = 0 the choice is the main segment.
+ *   R6  The Shouji bit-vector takes the chosen segment only when the segment
+ *       has strictly more zeros than the four bits it would overwrite
+ *       (Algorithm 1, step 2).
+ *   R7  Accept iff the number of ones in the Shouji bit-vector is at most E,
+ *       i.e. CZ(Shouji) >= m - E (Sec. 2.2.3, Algorithm 1, step 3).
+ *   R8  The base 'N' matches nothing, not even another 'N' (the paper is
+ *       silent on ambiguous bases).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+/* ---------------------------------------------------------------------- */
+/* Step 1: the neighborhood map (Sec. 2.2.1, Eq. 1).                       */
+/* map[(d + E) * m + c] = N entry of diagonal d at column c, d in [-E, E]. */
+/* ---------------------------------------------------------------------- */
+static int is_unknown_base(char x) { return x == 'N'; }
+
+void oracle_neighborhood_map(const char *P, const char *T, int m, int E,
+                             uint8_t *map)
+{
+    for (int d = -E; d <= E; ++d) {
+        for (int c = 0; c < m; ++c) {
+            int i = c - d;               /* index into P (row of N) */
+            uint8_t cell;
+            if (i < 0 || i >= m)
+                cell = 1;                /* R3: outside the band */
+            else if (is_unknown_base(P[i]) || is_unknown_base(T[c]))
+                cell = 1;                /* R8 */
+            else
+                cell = (P[i] == T[c]) ? 0 : 1;   /* Eq. 1 */
+            map[(size_t)(d + E) * m + c] = cell;
+        }
+    }
+}
+
+/* Algorithm 2: CZ counts the zeros of a bit-vector. */
+static int CZ(const uint8_t *bits, int len)
+{
+    int count = 0;
+    for (int k = 0; k < len; ++k)
+        if (bits[k] == 0)
+            count = count + 1;
+    return count;
+}
+
+/* The 4-bit segment of diagonal d in the window that starts at column c
+ * (R2, R4: columns past the end read as 1). */
+static void segment(const uint8_t *map, int m, int E, int d, int c,
+                    uint8_t seg[4])
+{
+    for (int k = 0; k < 4; ++k)
+        seg[k] = (c + k < m) ? map[(size_t)(d + E) * m + c + k] : 1;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Steps 1-3 for one pair.  Writes the Shouji bit-vector (m bytes, 0/1) to */
+/* S when S is not NULL and returns the number of ones in it (the edit     */
+/* estimate); the pair is accepted iff the return value is <= E.           */
+/* Returns -1 on an allocation failure or a bad argument.                  */
+/* ---------------------------------------------------------------------- */
+int oracle_shouji(const char *P, const char *T, int m, int E, uint8_t *S)
+{
+    if (m <= 0 || E < 0)
+        return -1;
+    uint8_t *map = (uint8_t *)malloc((size_t)(2 * E + 1) * m);
+    uint8_t *shouji = (uint8_t *)malloc((size_t)m);
+    if (!map || !shouji) {
+        free(map);
+        free(shouji);
+        return -1;
+    }
+
+    /* Step 1 */
+    oracle_neighborhood_map(P, T, m, E, map);
+
+    /* Step 2: the Shouji bit-vector starts as all ones. */
+    for (int c = 0; c < m; ++c)
+        shouji[c] = 1;
+
+    for (int c = 0; c < m; ++c) {            /* m search windows (R4) */
+        uint8_t Z[4], cand[4], cur[4];
+
+        /* Sec. 2.2.2 Step 1: the segment with the most zeros (R5). */
+        if (E == 0) {
+            segment(map, m, E, 0, c, Z);
+        } else {
+            segment(map, m, E, -1, c, Z);    /* lower_1 is examined first */
+            for (int j = 1; j <= E; ++j) {
+                for (int side = 0; side < 2; ++side) {
+                    int d = (side == 0) ? -j : +j;   /* lower_j, then upper_j */
+                    if (d == -1)
+                        continue;                    /* already the choice */
+                    segment(map, m, E, d, c, cand);
+                    int zc = CZ(cand, 4), zz = CZ(Z, 4);
+                    if (zc > zz || (zc == zz && Z[0] == 1 && cand[0] == 0))
+                        memcpy(Z, cand, 4);
+                }
+            }
+            segment(map, m, E, 0, c, cand);  /* main diagonal, strict */
+            if (CZ(cand, 4) > CZ(Z, 4))
+                memcpy(Z, cand, 4);
+        }
+
+        /* Sec. 2.2.2 Step 2: keep Z if it holds more zeros (R6). */
+        for (int k = 0; k < 4; ++k)
+            cur[k] = (c + k < m) ? shouji[c + k] : 1;
+        if (CZ(Z, 4) > CZ(cur, 4))
+            for (int k = 0; k < 4; ++k)
+                if (c + k < m)
+                    shouji[c + k] = Z[k];
+    }
+
+    /* Step 3 (Sec. 2.2.3): count the ones. */
+    int ones = m - CZ(shouji, m);
+    if (S)
+        memcpy(S, shouji, (size_t)m);
+    free(map);
+    free(shouji);
+    return ones;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Global edit distance (Levenshtein; unit-cost substitutions, insertions  */
+/* and deletions, end to end), by the full dynamic-programming table.  It  */
+/* is the ground truth the paper takes from Edlib in its global mode when  */
+/* it counts false accepts and false rejects (Sec. 3.2).                   */
+/* ---------------------------------------------------------------------- */
+int oracle_edit_distance(const char *a, int la, const char *b, int lb)
+{
+    int *prev = (int *)malloc(sizeof(int) * (size_t)(lb + 1));
+    int *next = (int *)malloc(sizeof(int) * (size_t)(lb + 1));
+    if (!prev || !next) {
+        free(prev);
+        free(next);
+        return -1;
+    }
+    for (int j = 0; j <= lb; ++j)
+        prev[j] = j;
+    for (int i = 1; i <= la; ++i) {
+        next[0] = i;
+        for (int j = 1; j <= lb; ++j) {
+            int sub = prev[j - 1] + (a[i - 1] == b[j - 1] ? 0 : 1);
+            int del = prev[j] + 1;
+            int ins = next[j - 1] + 1;
+            int best = sub < del ? sub : del;
+            next[j] = best < ins ? best : ins;
+        }
+        int *t = prev;
+        prev = next;
+        next = t;
+    }
+    int d = prev[lb];
+    free(prev);
+    free(next);
+    return d;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Batch driver: pairs (reads + i*stride, refs + i*stride), m bytes each.  */
+/* E_per_pair overrides E when not NULL.  accept[i] = 1/0, count[i] = the  */
+/* ones in the Shouji bit-vector (capped at 255 only by the type).  The    */
+/* pairs are split into contiguous ranges, one per thread.  Returns 0, or  */
+/* -1 on a failure.                                                        */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    const char *reads, *refs;
+    size_t stride;
+    int m, E;
+    const uint8_t *E_per_pair;
+    uint8_t *accept, *count;
+    size_t lo, hi;
+    int failed;
+} batch_job;
+
+static void *batch_worker(void *arg)
+{
+    batch_job *job = (batch_job *)arg;
+    for (size_t i = job->lo; i < job->hi; ++i) {
+        int E = job->E_per_pair ? job->E_per_pair[i] : job->E;
+        int ones = oracle_shouji(job->reads + i * job->stride,
+                                 job->refs + i * job->stride, job->m, E, NULL);
+        if (ones < 0) {
+            job->failed = 1;
+            return NULL;
+        }
+        if (job->accept)
+            job->accept[i] = (uint8_t)(ones <= E);
+        if (job->count)
+            job->count[i] = (uint8_t)ones;
+    }
+    return NULL;
+}
+
+int oracle_shouji_batch(const char *reads, const char *refs, size_t stride,
+                        int m, size_t n, int E, const uint8_t *E_per_pair,
+                        uint8_t *accept, uint8_t *count, int threads)
+{
+    if (threads < 1)
+        threads = 1;
+    if ((size_t)threads > n && n > 0)
+        threads = (int)n;
+    batch_job *jobs = (batch_job *)calloc((size_t)threads, sizeof(batch_job));
+    pthread_t *tids = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !tids) {
+        free(jobs);
+        free(tids);
+        return -1;
+    }
+    size_t per = n / (size_t)threads, extra = n % (size_t)threads, at = 0;
+    for (int t = 0; t < threads; ++t) {
+        size_t len = per + ((size_t)t < extra ? 1 : 0);
+        jobs[t] = (batch_job){reads, refs, stride, m, E, E_per_pair,
+                              accept, count, at, at + len, 0};
+        at += len;
+    }
+    int failed = 0;
+    if (threads == 1) {
+        batch_worker(&jobs[0]);
+    } else {
+        for (int t = 0; t < threads; ++t)
+            if (pthread_create(&tids[t], NULL, batch_worker, &jobs[t]) != 0)
+                jobs[t].failed = 2;
+        for (int t = 0; t < threads; ++t)
+            if (jobs[t].failed != 2)
+                pthread_join(tids[t], NULL);
+    }
+    for (int t = 0; t < threads; ++t)
+        failed |= jobs[t].failed;
+    free(jobs);
+    free(tids);
+    return failed ? -1 : 0;
+}
