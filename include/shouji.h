@@ -1,0 +1,182 @@
+/*
+ * shouji.h -- C ABI of libshouji.so, a GB300 (sm_103a) implementation of the
+ * Shouji pre-alignment filter (Alser et al., arXiv 1809.07858).
+ *
+ * Problem statement (Sec. 2.2 and Algorithm 1 of the paper): for a pair of
+ * equal-length sequences, a text T (the reference segment) and a pattern P
+ * (the read), and an edit distance threshold E, decide 1 = "similar,
+ * alignment needed" or 0 = "dissimilar".  The filter builds the 2E+1
+ * diagonal bit-vectors of the neighborhood map (Sec. 2.2.1, Eq. 1), slides
+ * a 4-column search window to pick the diagonal segment with the most zeros
+ * (Sec. 2.2.2), keeps the chosen segments in the Shouji bit-vector, counts
+ * its ones and accepts iff that count is at most E (Sec. 2.2.3).  Results
+ * come back one bit per pair, in input order (Sec. 2.3).
+ *
+ * Conventions shared by every call
+ *   - Device pointers are CUDA global memory of the current device, owned by
+ *     the caller.  The compute calls never allocate.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls are asynchronous on that stream: a return of
+ *     SHOUJI_OK means the work was launched; results are valid once the
+ *     stream has reached that point.
+ *   - Arguments are checked on the host; a bad one returns SHOUJI_EINVAL and
+ *     launches nothing.  A CUDA launch failure returns SHOUJI_ECUDA (the CUDA
+ *     error code is kept in shouji_last_cuda_error()).  Nothing aborts, traps
+ *     or exits.
+ *   - n = 0 pairs is valid and does nothing.
+ *   - Bases are the uppercase ASCII letters A, C, G, T and N.  An 'N' never
+ *     matches anything, another 'N' included, when its sequence was packed
+ *     with an N mask; without one it is read as 'G'.  Other bytes are not
+ *     checked: they are read through their bits 1-2 like the four bases.
+ *
+ * Packed ("bit-sliced") sequence layout, produced by shouji_pack and read by
+ * shouji_filter.  Sequences are grouped into tiles of SHOUJI_TILE = 1024 =
+ * 32 lanes x 32 bits.  Sequence s lives in tile t = s / 1024, lane
+ * l = (s % 1024) / 32, bit b = s % 32.  For position p (0 <= p < m) the
+ * base is a 2-bit code (A=00, C=01, G=11, T=10; hi bit, lo bit), stored as
+ *     packed[(((size_t)t * m + p) * 32 + l) * 2 + 0]  bit b = hi bit,
+ *     packed[(((size_t)t * m + p) * 32 + l) * 2 + 1]  bit b = lo bit,
+ * and the optional N mask as
+ *     nmask[((size_t)t * m + p) * 32 + l]             bit b = base is 'N'.
+ * One 32-bit word thus holds one position of 32 sequences: the filter works
+ * on 32 pairs per instruction.  Sizes: shouji_packed_words() and
+ * shouji_nmask_words().  Bits of the sequences past n in the last tile are
+ * written as zeros.
+ */
+#ifndef SHOUJI_H
+#define SHOUJI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SHOUJI_OK = 0,
+    SHOUJI_EINVAL = 1,   /* bad argument; nothing launched */
+    SHOUJI_ENOMEM = 2,   /* an allocation failed (pipeline creation only) */
+    SHOUJI_ECUDA = 3,    /* a CUDA call failed; see shouji_last_cuda_error() */
+    SHOUJI_ETIMEOUT = 4  /* a host wait passed its deadline */
+} shouji_status;
+
+#define SHOUJI_TILE 1024 /* sequences per packed tile */
+#define SHOUJI_MAX_M 255 /* longest sequence; the per-pair count fits a uint8 */
+#define SHOUJI_MAX_E 31  /* largest edit distance threshold (63 diagonals) */
+
+/* Human-readable name of a status code (static storage). */
+const char *shouji_status_string(shouji_status s);
+
+/* The cudaError_t of the last failed CUDA call made by this library on the
+ * calling host thread (0 when none). */
+int shouji_last_cuda_error(void);
+
+/* Number of uint32 words of a packed 2-bit array for n sequences of length
+ * m: ceil(n / 1024) * m * 64. */
+size_t shouji_packed_words(size_t n, uint32_t m);
+
+/* Number of uint32 words of an N mask for n sequences of length m:
+ * ceil(n / 1024) * m * 32. */
+size_t shouji_nmask_words(size_t n, uint32_t m);
+
+/*
+ * shouji_pack -- ASCII sequences to the packed bit-sliced layout.
+ *
+ * The FPGA design of the paper compares bases with XOR on an encoded form of
+ * the sequences (Sec. 2.3); this call produces the encoded form once, so a
+ * set of sequences can be filtered at many thresholds.
+ *
+ *   seqs    device, n rows of m bytes; row i starts at seqs + i * stride.
+ *   stride  bytes between rows, >= m.
+ *   n       number of sequences.
+ *   m       sequence length, 1 <= m <= SHOUJI_MAX_M.
+ *   packed  device, shouji_packed_words(n, m) words (layout above); written.
+ *   nmask   device, shouji_nmask_words(n, m) words, or NULL to encode 'N'
+ *           as 'G' (no mask).
+ * Errors: SHOUJI_EINVAL for NULL seqs/packed (with n > 0), m out of range,
+ * stride < m; SHOUJI_ECUDA on a launch failure.
+ */
+shouji_status shouji_pack(const uint8_t *seqs, uint64_t stride, size_t n,
+                          uint32_t m, uint32_t *packed, uint32_t *nmask,
+                          void *stream);
+
+/*
+ * shouji_filter -- the Shouji filter on n_pairs packed pairs (read i =
+ * pattern P, reference i = text T, both of length m).
+ *
+ * Per pair (Sec. 2.2; readings of the paper where it is silent or garbled
+ * are fixed as follows): diagonal d in [-E, E] holds at column c the
+ * mismatch bit of P[c-d] against T[c] (Eq. 1), 1 outside the band; window c
+ * (c = 0..m-1) covers columns c..c+3, columns past the end read as 1; the
+ * window's segment is chosen among lower_1, upper_1, ..., lower_E, upper_E
+ * by most zeros, a tie going to the first segment that starts with a zero,
+ * and the main diagonal replaces the choice only with strictly more zeros;
+ * the Shouji bit-vector (all ones at the start) takes the chosen segment
+ * only if it has strictly more zeros than the bits it replaces; the pair is
+ * accepted iff the vector holds at most E ones.
+ *
+ *   reads, refs   device, packed (shouji_packed_words(n_pairs, m) words).
+ *   reads_nmask,  device N masks of reads and refs (shouji_nmask_words), or
+ *   refs_nmask    both NULL.
+ *   m             1 <= m <= SHOUJI_MAX_M (the length both were packed with).
+ *   n_pairs       number of pairs.
+ *   E             0 <= E <= SHOUJI_MAX_E.  With E_per_pair it is the upper
+ *                 bound of the per-pair thresholds (the work per pair grows
+ *                 with it: 2E+1 diagonals, Eq. 2 of the paper).
+ *   E_per_pair    device uint8[n_pairs] with every value <= E, or NULL.
+ *                 Values above E are treated as E.
+ *   out_accept    device uint32[ceil(n_pairs / 32)]: bit i % 32 of word
+ *                 i / 32 = 1 iff pair i is accepted; bits past n_pairs = 0.
+ *   out_count     device uint8[n_pairs] = ones in pair i's Shouji bit-vector
+ *                 (its edit estimate), or NULL.
+ *   out_vectors   device, shouji_nmask_words(n_pairs, m) words, or NULL:
+ *                 the Shouji bit-vectors themselves, bit-sliced like an N
+ *                 mask (bit b of word ((t*m + c)*32 + l) = column c of pair
+ *                 1024t + 32l + b).
+ * Errors: SHOUJI_EINVAL for NULL reads/refs/out_accept (with n_pairs > 0),
+ * only one N mask given, m or E out of range; SHOUJI_ECUDA on a launch
+ * failure.
+ */
+shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
+                            const uint32_t *reads_nmask,
+                            const uint32_t *refs_nmask, uint32_t m,
+                            size_t n_pairs, int E, const uint8_t *E_per_pair,
+                            uint32_t *out_accept, uint8_t *out_count,
+                            uint32_t *out_vectors, void *stream);
+
+/*
+ * shouji_compact_workspace_size -- bytes of device workspace that
+ * shouji_compact needs for n_pairs pairs (0 for n_pairs = 0).
+ */
+size_t shouji_compact_workspace_size(size_t n_pairs);
+
+/*
+ * shouji_compact -- indices of the accepted pairs, in input order.
+ *
+ * The paper's accelerator returns one result bit per pair in input order
+ * and the host picks the survivors (Sec. 2.3); this call does that
+ * selection on the device.
+ *
+ *   accept      device uint32[ceil(n_pairs / 32)], as written by
+ *               shouji_filter (bits past n_pairs are ignored).
+ *   n_pairs     number of pairs, < 2^32.
+ *   out_idx     device uint32[n_pairs] (worst case); the first *out_n
+ *               entries receive the accepted pair indices in increasing order.
+ *   out_n       device uint32[1]: number of accepted pairs.
+ *   workspace   device scratch of at least workspace_bytes >=
+ *               shouji_compact_workspace_size(n_pairs) bytes, 16-byte
+ *               aligned; its contents on entry do not matter.
+ * Errors: SHOUJI_EINVAL for NULL pointers (with n_pairs > 0), n_pairs >=
+ * 2^32, a short or misaligned workspace; SHOUJI_ECUDA on a launch failure.
+ */
+shouji_status shouji_compact(const uint32_t *accept, size_t n_pairs,
+                             uint32_t *out_idx, uint32_t *out_n,
+                             void *workspace, size_t workspace_bytes,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHOUJI_H */

@@ -1,2 +1,209 @@
-"""ctypes binding of libshouji.so (filled in with the C-ABI)."""
-__all__ = []
+"""ctypes binding of libshouji.so: argument marshalling only.
+
+Every function here forwards to the C ABI declared in ``include/shouji.h``
+with the same name; torch tensors supply device memory and the current CUDA
+stream.  No step of the filter runs in Python.  The library is loaded on
+first use and a missing or unloadable library raises ``ShoujiError`` (there
+is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libshouji.so")
+
+SHOUJI_TILE = 1024
+SHOUJI_MAX_M = 255
+SHOUJI_MAX_E = 31
+
+__all__ = [
+    "ShoujiError", "SHOUJI_TILE", "SHOUJI_MAX_M", "SHOUJI_MAX_E", "LIB_PATH",
+    "load_library", "shouji_status_string", "shouji_last_cuda_error",
+    "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
+    "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
+    "accept_to_bool",
+]
+
+_lib = None
+
+
+class ShoujiError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = "%s: %s" % (where, shouji_status_string(status) if _lib else status)
+        if status == 3 and _lib is not None:
+            msg += " (cudaError %d)" % _lib.shouji_last_cuda_error()
+        super().__init__(msg)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libshouji.so (built in-tree by ``paper_1809_07858_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ShoujiError(-1, "libshouji.so not built at %s (run __graft_entry__.build())" % path)
+    lib = ctypes.CDLL(path)
+    vp, sz, u32, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64
+    lib.shouji_status_string.argtypes = [ctypes.c_int]
+    lib.shouji_status_string.restype = ctypes.c_char_p
+    lib.shouji_last_cuda_error.argtypes = []
+    lib.shouji_last_cuda_error.restype = ctypes.c_int
+    lib.shouji_packed_words.argtypes = [sz, u32]
+    lib.shouji_packed_words.restype = sz
+    lib.shouji_nmask_words.argtypes = [sz, u32]
+    lib.shouji_nmask_words.restype = sz
+    lib.shouji_pack.argtypes = [vp, u64, sz, u32, vp, vp, vp]
+    lib.shouji_pack.restype = ctypes.c_int
+    lib.shouji_filter.argtypes = [vp, vp, vp, vp, u32, sz, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.shouji_filter.restype = ctypes.c_int
+    lib.shouji_compact_workspace_size.argtypes = [sz]
+    lib.shouji_compact_workspace_size.restype = sz
+    lib.shouji_compact.argtypes = [vp, sz, vp, vp, vp, sz, vp]
+    lib.shouji_compact.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def shouji_status_string(status: int) -> str:
+    return load_library().shouji_status_string(int(status)).decode()
+
+
+def shouji_last_cuda_error() -> int:
+    return load_library().shouji_last_cuda_error()
+
+
+def shouji_packed_words(n: int, m: int) -> int:
+    return load_library().shouji_packed_words(n, m)
+
+
+def shouji_nmask_words(n: int, m: int) -> int:
+    return load_library().shouji_nmask_words(n, m)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise ShoujiError(status, where)
+
+
+def shouji_pack(seqs, m: int, *, n: int | None = None, stride: int | None = None,
+                with_n: bool = False, packed=None, nmask=None, stream=None):
+    """ASCII sequences -> packed bit-sliced planes (and N mask).
+
+    ``seqs``: CUDA uint8 tensor, (n, stride) or flat with ``n`` and ``stride``.
+    Returns ``(packed, nmask)`` (``nmask`` is None unless ``with_n``).
+    """
+    torch = _torch()
+    lib = load_library()
+    if seqs.dim() == 2:
+        n = seqs.shape[0] if n is None else n
+        stride = seqs.shape[1] if stride is None else stride
+    assert n is not None and stride is not None
+    dev = seqs.device
+    if packed is None:
+        packed = torch.empty(max(1, lib.shouji_packed_words(n, m)), dtype=torch.int32, device=dev)
+    if with_n and nmask is None:
+        nmask = torch.empty(max(1, lib.shouji_nmask_words(n, m)), dtype=torch.int32, device=dev)
+    _check(lib.shouji_pack(_ptr(seqs), stride, n, m, _ptr(packed),
+                           _ptr(nmask) if with_n else None, _stream(stream)), "shouji_pack")
+    return packed, (nmask if with_n else None)
+
+
+def shouji_filter(reads, refs, m: int, n_pairs: int, E: int, *, reads_nmask=None,
+                  refs_nmask=None, E_per_pair=None, out_accept=None, out_count=None,
+                  count: bool = True, out_vectors=None, vectors: bool = False,
+                  stream=None):
+    """Filter packed pairs.  Returns ``(accept_words, count, vectors)``.
+
+    ``accept_words``: int32 tensor of ceil(n_pairs/32) words (bit i%32 of word
+    i//32 = pair i accepted); ``count``: uint8[n_pairs] or None; ``vectors``:
+    bit-sliced Shouji bit-vectors or None.
+    """
+    torch = _torch()
+    lib = load_library()
+    dev = reads.device
+    if out_accept is None:
+        out_accept = torch.empty(max(1, (n_pairs + 31) // 32), dtype=torch.int32, device=dev)
+    if out_count is None and count:
+        out_count = torch.empty(max(1, n_pairs), dtype=torch.uint8, device=dev)
+    if out_vectors is None and vectors:
+        out_vectors = torch.empty(max(1, lib.shouji_nmask_words(n_pairs, m)), dtype=torch.int32,
+                                  device=dev)
+    _check(lib.shouji_filter(_ptr(reads), _ptr(refs), _ptr(reads_nmask), _ptr(refs_nmask),
+                             m, n_pairs, E, _ptr(E_per_pair), _ptr(out_accept),
+                             _ptr(out_count), _ptr(out_vectors), _stream(stream)),
+           "shouji_filter")
+    return out_accept, out_count, out_vectors
+
+
+def shouji_compact_workspace_size(n_pairs: int) -> int:
+    return load_library().shouji_compact_workspace_size(n_pairs)
+
+
+def shouji_compact(accept, n_pairs: int, *, out_idx=None, out_n=None, workspace=None,
+                   stream=None):
+    """Indices of accepted pairs in input order.  Returns ``(idx, n_dev)``;
+    the first ``int(n_dev)`` entries of ``idx`` are valid."""
+    torch = _torch()
+    lib = load_library()
+    dev = accept.device
+    if out_idx is None:
+        out_idx = torch.empty(max(1, n_pairs), dtype=torch.int32, device=dev)
+    if out_n is None:
+        out_n = torch.empty(1, dtype=torch.int32, device=dev)
+    ws_bytes = lib.shouji_compact_workspace_size(n_pairs)
+    if workspace is None:
+        workspace = torch.empty(max(16, ws_bytes), dtype=torch.uint8, device=dev)
+    _check(lib.shouji_compact(_ptr(accept), n_pairs, _ptr(out_idx), _ptr(out_n),
+                              _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _stream(stream)), "shouji_compact")
+    return out_idx, out_n
+
+
+def accept_to_bool(accept_words, n_pairs: int):
+    """Expand accept words to a bool tensor of n_pairs entries (on the words' device)."""
+    torch = _torch()
+    w = accept_words[: (n_pairs + 31) // 32].to(torch.int64) & 0xFFFFFFFF
+    bits = (w.unsqueeze(1) >> torch.arange(32, device=w.device)) & 1
+    return bits.reshape(-1)[:n_pairs].bool()
+
+
+def filter_pairs(reads, refs, E: int, *, with_n: bool | None = None, E_per_pair=None,
+                 stream=None):
+    """Pack and filter (n, m) uint8 CUDA tensors of reads and references.
+
+    Returns ``(accept_bool[n], count_uint8[n])``.  ``with_n`` defaults to
+    checking whether any 'N' is present.
+    """
+    n, m = reads.shape
+    assert refs.shape == reads.shape
+    if with_n is None:
+        with_n = bool(((reads == 78).any() | (refs == 78).any()).item())
+    pr, nr = shouji_pack(reads, m, with_n=with_n, stream=stream)
+    pt, nt = shouji_pack(refs, m, with_n=with_n, stream=stream)
+    acc, cnt, _ = shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
+                                E_per_pair=E_per_pair, stream=stream)
+    return accept_to_bool(acc, n), cnt[:n]

@@ -1,0 +1,130 @@
+// The C ABI of libshouji.so (declared in include/shouji.h): argument checks,
+// status codes and dispatch to the kernels.  Nothing here computes a result.
+#include "shouji_internal.cuh"
+
+namespace shouji {
+
+static thread_local int g_last_cuda_error = 0;
+
+shouji_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return SHOUJI_OK;
+    g_last_cuda_error = (int)e;
+    return SHOUJI_ECUDA;
+}
+
+namespace {
+
+using LaunchFn = cudaError_t (*)(const FilterArgs &, cudaStream_t);
+
+
+constexpr LaunchFn kFilter[SHOUJI_MAX_E + 1] = {
+    &launch_filter_E<0>,  &launch_filter_E<1>,  &launch_filter_E<2>,  &launch_filter_E<3>,
+    &launch_filter_E<4>,  &launch_filter_E<5>,  &launch_filter_E<6>,  &launch_filter_E<7>,
+    &launch_filter_E<8>,  &launch_filter_E<9>,  &launch_filter_E<10>, &launch_filter_E<11>,
+    &launch_filter_E<12>, &launch_filter_E<13>, &launch_filter_E<14>, &launch_filter_E<15>,
+    &launch_filter_E<16>, &launch_filter_E<17>, &launch_filter_E<18>, &launch_filter_E<19>,
+    &launch_filter_E<20>, &launch_filter_E<21>, &launch_filter_E<22>, &launch_filter_E<23>,
+    &launch_filter_E<24>, &launch_filter_E<25>, &launch_filter_E<26>, &launch_filter_E<27>,
+    &launch_filter_E<28>, &launch_filter_E<29>, &launch_filter_E<30>, &launch_filter_E<31>,
+};
+
+}  // namespace
+
+cudaError_t launch_filter(const FilterArgs &a, int E, cudaStream_t s)
+{
+    return kFilter[E](a, s);
+}
+
+}  // namespace shouji
+
+using namespace shouji;
+
+extern "C" {
+
+const char *shouji_status_string(shouji_status s)
+{
+    switch (s) {
+    case SHOUJI_OK: return "SHOUJI_OK";
+    case SHOUJI_EINVAL: return "SHOUJI_EINVAL: invalid argument";
+    case SHOUJI_ENOMEM: return "SHOUJI_ENOMEM: allocation failed";
+    case SHOUJI_ECUDA: return "SHOUJI_ECUDA: CUDA call failed";
+    case SHOUJI_ETIMEOUT: return "SHOUJI_ETIMEOUT: deadline passed";
+    }
+    return "SHOUJI: unknown status";
+}
+
+int shouji_last_cuda_error(void) { return g_last_cuda_error; }
+
+size_t shouji_packed_words(size_t n, uint32_t m) { return tiles_of(n) * (size_t)m * 64; }
+
+size_t shouji_nmask_words(size_t n, uint32_t m) { return tiles_of(n) * (size_t)m * 32; }
+
+shouji_status shouji_pack(const uint8_t *seqs, uint64_t stride, size_t n, uint32_t m,
+                          uint32_t *packed, uint32_t *nmask, void *stream)
+{
+    if (m < 1 || m > SHOUJI_MAX_M || stride < m)
+        return SHOUJI_EINVAL;
+    if (n == 0)
+        return SHOUJI_OK;
+    if (!seqs || !packed)
+        return SHOUJI_EINVAL;
+    return cuda_status(launch_pack(seqs, stride, n, (int)m, packed, nmask, (cudaStream_t)stream));
+}
+
+shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
+                            const uint32_t *reads_nmask, const uint32_t *refs_nmask,
+                            uint32_t m, size_t n_pairs, int E, const uint8_t *E_per_pair,
+                            uint32_t *out_accept, uint8_t *out_count, uint32_t *out_vectors,
+                            void *stream)
+{
+    if (m < 1 || m > SHOUJI_MAX_M || E < 0 || E > SHOUJI_MAX_E)
+        return SHOUJI_EINVAL;
+    if ((reads_nmask == nullptr) != (refs_nmask == nullptr))
+        return SHOUJI_EINVAL;
+    if (n_pairs == 0)
+        return SHOUJI_OK;
+    if (!reads || !refs || !out_accept)
+        return SHOUJI_EINVAL;
+    if ((uintptr_t)reads % 8 || (uintptr_t)refs % 8)
+        return SHOUJI_EINVAL;
+    FilterArgs a;
+    a.reads = reinterpret_cast<const uint2 *>(reads);
+    a.refs = reinterpret_cast<const uint2 *>(refs);
+    a.reads_n = reads_nmask;
+    a.refs_n = refs_nmask;
+    a.E_per_pair = E_per_pair;
+    a.accept = out_accept;
+    a.count = out_count;
+    a.vectors = out_vectors;
+    a.n_pairs = n_pairs;
+    a.m = (int)m;
+    return cuda_status(launch_filter(a, E, (cudaStream_t)stream));
+}
+
+size_t shouji_compact_workspace_size(size_t n_pairs)
+{
+    return n_pairs ? compact_workspace_bytes(n_pairs) : 0;
+}
+
+shouji_status shouji_compact(const uint32_t *accept, size_t n_pairs, uint32_t *out_idx,
+                             uint32_t *out_n, void *workspace, size_t workspace_bytes,
+                             void *stream)
+{
+    if (n_pairs >= ((size_t)1 << 32))
+        return SHOUJI_EINVAL;
+    if (n_pairs == 0) {
+        if (out_n)
+            return cuda_status(cudaMemsetAsync(out_n, 0, sizeof(uint32_t), (cudaStream_t)stream));
+        return SHOUJI_OK;
+    }
+    if (!accept || !out_idx || !out_n || !workspace)
+        return SHOUJI_EINVAL;
+    if (workspace_bytes < compact_workspace_bytes(n_pairs) || (uintptr_t)workspace % 16)
+        return SHOUJI_EINVAL;
+    return cuda_status(launch_compact(accept, n_pairs, out_idx, out_n, workspace,
+                                      (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,371 @@
+// The Shouji filter kernel (arXiv 1809.07858, Sec. 2.2), bit-sliced across
+// pairs: one thread filters 32 pairs at once.  Every 32-bit register holds
+// one bit position of 32 pairs (bit b = pair b of the thread's group), so a
+// single LOP3 advances all 32 pairs; no instruction depends on the data, and
+// the per-pair serial chain of the paper's Step 2 becomes 32 pairs per step.
+//
+// Per window c (c = 0..m-1) and pair, the paper's work is:
+//   Step 1 (neighborhood map, Eq. 1): diagonal d in [-E, E] has, at column p,
+//     the mismatch bit M_d[p] = [P[p-d] != T[p]] (1 outside the band, 1 past
+//     the end).  With the 2-bit codes, M = (Th ^ Ph) | (Tl ^ Pl) (| N masks).
+//   Step 2a (search window, Sec. 2.2.2): the segment M_d[c..c+3] with the
+//     most zeros, ties to the first with a leading zero, in the order lower_1,
+//     upper_1, ..., lower_E, upper_E, then the main diagonal with strictly
+//     more zeros.  Keys are compared without counting: with a = candidate,
+//     b = current choice, "a wins" <=> 2(ones(b) - ones(a)) + 3(b0 - a0) > 0,
+//     evaluated on the full-adder sum/carry of bits 1..3 of each segment.
+//   Step 2b (Shouji bit-vector): S starts as all ones; window c writes Z into
+//     S[c..c+3] iff Z has strictly more zeros.  Only windows >= c can write
+//     S[c+3], so before window c the live state is (S[c], S[c+1], S[c+2]) and
+//     S[c+3] = 1; after window c, S[c] is final.  The test "Z has more zeros"
+//     is ones(Z) <= ones(S[c..c+2]), again from full-adder bits.
+//   Step 3 (Sec. 2.2.3): the final S bits are summed in a bit-sliced 8-bit
+//     counter; accept iff count <= E.
+//
+// Windows are processed in chunks of U; a chunk recomputes the U+3 map
+// columns it needs for each diagonal from the packed words (loads go through
+// the read-only cache; the footprint per warp is a few KB).
+#pragma once
+
+#include "shouji_internal.cuh"
+
+namespace shouji {
+namespace filt {
+
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c)
+{
+    return (a & b) | (a & c) | (b & c);
+}
+
+// Current choice of one window: bits z0..z3 (1 = mismatch) and the full-adder
+// sum/carry of z1..z3 (ones(z) = z0 + zs + 2*zc).
+struct Pick {
+    uint32_t z0, z1, z2, z3, zs, zc;
+};
+
+__device__ __forceinline__ Pick make_pick(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3)
+{
+    Pick p;
+    p.z0 = a0;
+    p.z1 = a1;
+    p.z2 = a2;
+    p.z3 = a3;
+    p.zs = a1 ^ a2 ^ a3;
+    p.zc = maj3(a1, a2, a3);
+    return p;
+}
+
+// Offer candidate segment a (a0..a3) to the window's current choice b under the
+// rule "more zeros wins; on a tie a leading zero beats a leading one".
+// With u = ones(b1..b3) + zeros(a1..a3) in [0, 6] and v = b0 + (1 - a0):
+// a wins <=> 2u + 3v >= 10, i.e. v=2: u>=2;  v=1: u>=4;  v=0: u>=5.
+__device__ __forceinline__ void offer(Pick &b, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3)
+{
+    const uint32_t as = a1 ^ a2 ^ a3;
+    const uint32_t ac = maj3(a1, a2, a3);
+    // zeros(a1..a3) = ~as + 2 ~ac ; u = x0 + 2 (x1 + b.zc + ~ac) = x0 + 2 y0 + 4 y1
+    const uint32_t x0 = b.zs ^ ~as;
+    const uint32_t x1 = b.zs & ~as;
+    const uint32_t y0 = x1 ^ b.zc ^ ~ac;
+    const uint32_t y1 = maj3(x1, b.zc, ~ac);
+    const uint32_t win = (y1 & (b.z0 | ~a0 | x0 | y0)) | (~y1 & b.z0 & ~a0 & y0);
+    b.z0 = (win & a0) | (~win & b.z0);
+    b.z1 = (win & a1) | (~win & b.z1);
+    b.z2 = (win & a2) | (~win & b.z2);
+    b.z3 = (win & a3) | (~win & b.z3);
+    b.zs = (win & as) | (~win & b.zs);
+    b.zc = (win & ac) | (~win & b.zc);
+}
+
+// The main diagonal replaces the choice only with strictly more zeros:
+// ones(z) > ones(main).
+__device__ __forceinline__ void offer_main(Pick &b, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3)
+{
+    const uint32_t as = a1 ^ a2 ^ a3;
+    const uint32_t ac = maj3(a1, a2, a3);
+    // 3-bit popcounts: ones(z) = (p2 p1 p0), ones(main) = (q2 q1 q0)
+    const uint32_t p0 = b.z0 ^ b.zs, pk = b.z0 & b.zs;
+    const uint32_t p1 = b.zc ^ pk, p2 = b.zc & pk;
+    const uint32_t q0 = a0 ^ as, qk = a0 & as;
+    const uint32_t q1 = ac ^ qk, q2 = ac & qk;
+    const uint32_t gt = (p2 & ~q2) |
+                        (~(p2 ^ q2) & ((p1 & ~q1) | (~(p1 ^ q1) & p0 & ~q0)));
+    b.z0 = (gt & a0) | (~gt & b.z0);
+    b.z1 = (gt & a1) | (~gt & b.z1);
+    b.z2 = (gt & a2) | (~gt & b.z2);
+    b.z3 = (gt & a3) | (~gt & b.z3);
+    b.zs = (gt & as) | (~gt & b.zs);
+    b.zc = (gt & ac) | (~gt & b.zc);
+}
+
+// Bit-sliced 8-bit counter += x (3-bit value x2 x1 x0).
+__device__ __forceinline__ void counter_add3(uint32_t (&C)[8], uint32_t x0, uint32_t x1, uint32_t x2)
+{
+    uint32_t k = C[0] & x0;
+    C[0] ^= x0;
+    uint32_t t = C[1] ^ x1;
+    uint32_t k2 = maj3(C[1], x1, k);
+    C[1] = t ^ k;
+    k = k2;
+    t = C[2] ^ x2;
+    k2 = maj3(C[2], x2, k);
+    C[2] = t ^ k;
+    k = k2;
+#pragma unroll
+    for (int i = 3; i < 8; ++i) {
+        const uint32_t c = C[i] & k;
+        C[i] ^= k;
+        k = c;
+    }
+}
+
+// Per-thread view of the packed data of one group of 32 pairs.
+struct View {
+    const uint2 *rd, *rf;       // position p at [p * 32]
+    const uint32_t *rdn, *rfn;  // N masks (may be null)
+    uint32_t *vec;              // Shouji vectors out (may be null), [c * 32]
+    int m;
+};
+
+// One chunk of U windows starting at c0.
+//   BOUNDS: columns and read positions may fall outside [0, m) (edge chunks);
+//           an unbounded chunk needs c0 - E >= 0 and c0 + U + 2 + E < m.
+//   MASKS:  N masks and/or per-pair thresholds are present.
+template <int E, int U, bool BOUNDS, bool MASKS>
+__device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[E + 1], int c0,
+                                      uint32_t &s0, uint32_t &s1, uint32_t &s2,
+                                      uint32_t (&C)[8])
+{
+    constexpr int NC = U + 3;        // columns c0 .. c0+U+2
+    constexpr int NR = NC + 2 * E;   // read positions c0-E .. c0+U+2+E
+    uint32_t th[NC], tl[NC], tx[MASKS ? NC : 1];
+    uint32_t rh[NR], rl[NR], rx[MASKS ? NR : 1];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int p = c0 + k;
+        const bool ok = !BOUNDS || p < v.m;
+        const uint2 w = ok ? __ldg(v.rf + (size_t)p * 32) : make_uint2(0u, 0u);
+        th[k] = w.x;
+        tl[k] = w.y;
+        if constexpr (MASKS)
+            tx[k] = (ok && v.rfn) ? __ldg(v.rfn + (size_t)p * 32) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int q = c0 - E + i;
+        const bool ok = !BOUNDS || (q >= 0 && q < v.m);
+        const uint2 w = ok ? __ldg(v.rd + (size_t)q * 32) : make_uint2(0u, 0u);
+        rh[i] = w.x;
+        rl[i] = w.y;
+        if constexpr (MASKS)
+            rx[i] = (ok && v.rdn) ? __ldg(v.rdn + (size_t)q * 32) : 0u;
+    }
+
+    // Mismatch bits of diagonal d at the chunk's column k.
+    auto column = [&](int d, int k) -> uint32_t {
+        const int i = k - d + E;
+        uint32_t x = (th[k] ^ rh[i]) | (tl[k] ^ rl[i]);
+        if constexpr (MASKS)
+            x |= tx[k] | rx[i] | inactive[d < 0 ? -d : d];
+        if constexpr (BOUNDS) {
+            const int p = c0 + k, q = c0 - E + i;
+            if (p >= v.m || q < 0 || q >= v.m)
+                x = ~0u;
+        }
+        return x;
+    };
+
+    Pick pick[U];
+    if constexpr (E == 0) {
+        uint32_t M[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            M[k] = column(0, k);
+#pragma unroll
+        for (int w = 0; w < U; ++w)
+            pick[w] = make_pick(M[w], M[w + 1], M[w + 2], M[w + 3]);
+    } else {
+        {
+            uint32_t M[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k)
+                M[k] = column(-1, k);
+#pragma unroll
+            for (int w = 0; w < U; ++w)
+                pick[w] = make_pick(M[w], M[w + 1], M[w + 2], M[w + 3]);
+        }
+#pragma unroll
+        for (int j = 1; j <= E; ++j) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int d = side ? j : -j;
+                if (d == -1)
+                    continue;
+                uint32_t M[NC];
+#pragma unroll
+                for (int k = 0; k < NC; ++k)
+                    M[k] = column(d, k);
+#pragma unroll
+                for (int w = 0; w < U; ++w)
+                    offer(pick[w], M[w], M[w + 1], M[w + 2], M[w + 3]);
+            }
+        }
+        uint32_t M[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            M[k] = column(0, k);
+#pragma unroll
+        for (int w = 0; w < U; ++w)
+            offer_main(pick[w], M[w], M[w + 1], M[w + 2], M[w + 3]);
+    }
+
+    // Step 2b: the Shouji bit-vector, window by window.
+    uint32_t out[U];
+#pragma unroll
+    for (int w = 0; w < U; ++w) {
+        const Pick &z = pick[w];
+        if (c0 + w < v.m) {
+            const uint32_t ns = ~(s0 ^ s1 ^ s2);    // parity of zeros(s0..s2)
+            const uint32_t nc = ~maj3(s0, s1, s2);  // carry of zeros(s0..s2)
+            const uint32_t w1 = maj3(z.z0, z.zs, ns);
+            const uint32_t upd = ~maj3(w1, z.zc, nc);  // ones(Z) <= ones(s0..s2)
+            out[w] = (upd & z.z0) | (~upd & s0);
+            s0 = (upd & z.z1) | (~upd & s1);
+            s1 = (upd & z.z2) | (~upd & s2);
+            s2 = z.z3 | ~upd;
+            if (v.vec)
+                v.vec[(size_t)(c0 + w) * 32] = out[w];
+        } else {
+            out[w] = 0u;
+        }
+    }
+    // Step 3: add the U final bits to the counter (U = 4: one 3-bit sum).
+#pragma unroll
+    for (int w = 0; w < U; w += 4) {
+        const uint32_t fs = out[w] ^ out[w + 1] ^ out[w + 2];
+        const uint32_t fc = maj3(out[w], out[w + 1], out[w + 2]);
+        const uint32_t x0 = fs ^ out[w + 3];
+        const uint32_t t = fs & out[w + 3];
+        counter_add3(C, x0, fc ^ t, fc & t);
+    }
+}
+
+template <int E, int U, bool MASKS>
+__global__ void __launch_bounds__(kThreads)
+filter_kernel(FilterArgs a)
+{
+    static_assert(U % 4 == 0, "U must be a multiple of 4");
+    const size_t g = (size_t)blockIdx.x * kThreads + threadIdx.x;  // group of 32 pairs
+    const size_t n_groups = groups_of(a.n_pairs);
+    if (g >= n_groups)
+        return;
+    const size_t tile = g / kLanes;
+    const int lane = (int)(g % kLanes);
+    const int m = a.m;
+    const size_t base = tile * (size_t)m * kLanes + lane;
+    const size_t first = g * 32;
+    const size_t left = a.n_pairs - first;
+
+    View v;
+    v.rd = a.reads + base;
+    v.rf = a.refs + base;
+    v.rdn = a.reads_n ? a.reads_n + base : nullptr;
+    v.rfn = a.refs_n ? a.refs_n + base : nullptr;
+    v.vec = a.vectors ? a.vectors + base : nullptr;
+    v.m = m;
+
+    // Per-pair thresholds: inactive[j] bit b = pair b's threshold is below j,
+    // so diagonals +-j are all mismatches for it (they can then never win).
+    uint32_t inactive[E + 1];
+#pragma unroll
+    for (int j = 0; j <= E; ++j)
+        inactive[j] = 0u;
+    if (MASKS && a.E_per_pair) {
+        for (int b = 0; b < 32 && (size_t)b < left; ++b) {
+            const int e = a.E_per_pair[first + b];
+#pragma unroll
+            for (int j = 1; j <= E; ++j)
+                inactive[j] |= (uint32_t)(e < j) << b;
+        }
+    }
+
+    uint32_t s0 = ~0u, s1 = ~0u, s2 = ~0u;
+    uint32_t C[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        C[i] = 0u;
+
+    if constexpr (MASKS) {
+        for (int c0 = 0; c0 < m; c0 += U)
+            chunk<E, U, true, true>(v, inactive, c0, s0, s1, s2, C);
+    } else {
+        for (int c0 = 0; c0 < m; c0 += U) {
+            if ((c0 - E >= 0) && (c0 + U + 2 + E < m))
+                chunk<E, U, false, false>(v, inactive, c0, s0, s1, s2, C);
+            else
+                chunk<E, U, true, false>(v, inactive, c0, s0, s1, s2, C);
+        }
+    }
+
+    // Per-pair counts and the accept word.
+    uint32_t acc = 0;
+    uint32_t cw[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b = 4 * q + u;
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                cnt |= ((C[k] >> b) & 1u) << k;
+            uint32_t thr = (uint32_t)E;
+            if (MASKS && a.E_per_pair && (size_t)b < left) {
+                const uint32_t e = a.E_per_pair[first + b];
+                thr = e < thr ? e : thr;
+            }
+            acc |= (uint32_t)(cnt <= thr) << b;
+            word |= cnt << (8 * u);
+        }
+        cw[q] = word;
+    }
+    if (left < 32)
+        acc &= (1u << left) - 1u;
+    a.accept[g] = acc;
+    if (a.count) {
+        if (left >= 32 && ((uintptr_t)(a.count + first) % 16 == 0)) {
+            uint4 *dst = reinterpret_cast<uint4 *>(a.count + first);
+            dst[0] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+            dst[1] = make_uint4(cw[4], cw[5], cw[6], cw[7]);
+        } else {
+            for (int b = 0; b < 32 && (size_t)b < left; ++b)
+                a.count[first + b] = (uint8_t)(cw[b >> 2] >> (8 * (b & 3)));
+        }
+    }
+}
+
+template <int E>
+cudaError_t launch_E(const FilterArgs &a, cudaStream_t s)
+{
+    constexpr int U = 4;
+    const size_t groups = groups_of(a.n_pairs);
+    const size_t blocks = (groups + kThreads - 1) / kThreads;
+    if (a.reads_n || a.E_per_pair)
+        filter_kernel<E, U, true><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    else
+        filter_kernel<E, U, false><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace filt
+
+template <int E>
+cudaError_t launch_filter_E(const FilterArgs &a, cudaStream_t s)
+{
+    return filt::launch_E<E>(a, s);
+}
+
+}  // namespace shouji

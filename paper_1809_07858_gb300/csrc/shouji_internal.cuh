@@ -1,0 +1,47 @@
+// Internal declarations shared by the translation units of libshouji.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "shouji.h"
+
+namespace shouji {
+
+constexpr int kLanes = 32;            // 32-bit words per tile position
+constexpr int kTile = 32 * kLanes;    // sequences per tile (SHOUJI_TILE)
+
+__host__ __device__ inline size_t tiles_of(size_t n) { return (n + kTile - 1) / kTile; }
+__host__ __device__ inline size_t groups_of(size_t n) { return (n + 31) / 32; }
+
+// Remember a failed CUDA call for shouji_last_cuda_error() and map it to a
+// status code.
+shouji_status cuda_status(cudaError_t e);
+
+// Launchers (argument checks are done by the C-ABI layer).
+cudaError_t launch_pack(const uint8_t *seqs, uint64_t stride, size_t n, int m,
+                        uint32_t *packed, uint32_t *nmask, cudaStream_t s);
+
+struct FilterArgs {
+    const uint2 *reads, *refs;               // packed pairs (hi, lo) words
+    const uint32_t *reads_n, *refs_n;        // N masks or null
+    const uint8_t *E_per_pair;               // per-pair thresholds or null
+    uint32_t *accept;                        // ceil(n/32) words
+    uint8_t *count;                          // n bytes or null
+    uint32_t *vectors;                       // bit-sliced Shouji vectors or null
+    size_t n_pairs;
+    int m;
+};
+cudaError_t launch_filter(const FilterArgs &a, int E, cudaStream_t s);
+
+// One launcher per threshold, defined in the per-range instantiation units.
+template <int E>
+cudaError_t launch_filter_E(const FilterArgs &a, cudaStream_t s);
+
+size_t compact_workspace_bytes(size_t n_pairs);
+cudaError_t launch_compact(const uint32_t *accept, size_t n_pairs,
+                           uint32_t *out_idx, uint32_t *out_n, void *workspace,
+                           cudaStream_t s);
+
+}  // namespace shouji

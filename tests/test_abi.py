@@ -1,0 +1,74 @@
+"""The C-ABI library loads and exports what include/shouji.h declares; host-side
+argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1809_07858_gb300 as sj
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "shouji.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(shouji_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for fn in ("shouji_pack", "shouji_filter", "shouji_compact",
+               "shouji_compact_workspace_size", "shouji_status_string"):
+        assert fn in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(sj.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_size_helpers():
+    assert sj.shouji_packed_words(0, 100) == 0
+    assert sj.shouji_packed_words(1, 100) == 100 * 64
+    assert sj.shouji_packed_words(1024, 100) == 100 * 64
+    assert sj.shouji_packed_words(1025, 100) == 2 * 100 * 64
+    assert sj.shouji_nmask_words(30_000_000, 100) == 29297 * 100 * 32
+    assert sj.shouji_compact_workspace_size(0) == 0
+    ws = sj.shouji_compact_workspace_size(30_000_000)
+    assert ws % 16 == 0 and ws >= 4 * ((30_000_000 // 32 + 4095) // 4096)
+
+
+def test_status_strings():
+    for s in range(5):
+        assert sj.shouji_status_string(s).startswith("SHOUJI")
+
+
+def test_host_argument_checks_return_einval():
+    lib = sj.load_library()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails its checks
+    EINVAL, OK = 1, 0
+    # pack: m out of range, stride < m, null pointers
+    assert lib.shouji_pack(fake, 100, 10, 0, fake, None, None) == EINVAL
+    assert lib.shouji_pack(fake, 300, 10, 256, fake, None, None) == EINVAL
+    assert lib.shouji_pack(fake, 99, 10, 100, fake, None, None) == EINVAL
+    assert lib.shouji_pack(None, 100, 10, 100, fake, None, None) == EINVAL
+    assert lib.shouji_pack(fake, 100, 10, 100, None, None, None) == EINVAL
+    assert lib.shouji_pack(None, 100, 0, 100, None, None, None) == OK   # n = 0
+    # filter: E range, m range, one-sided N mask, nulls, misalignment
+    assert lib.shouji_filter(fake, fake, None, None, 100, 10, -1, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_filter(fake, fake, None, None, 100, 10, 32, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_filter(fake, fake, None, None, 0, 10, 5, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_filter(fake, fake, fake, None, 100, 10, 5, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_filter(None, fake, None, None, 100, 10, 5, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_filter(fake, fake, None, None, 100, 10, 5, None, None, None, None, None) == EINVAL
+    assert lib.shouji_filter(ctypes.c_void_p(0x1004), fake, None, None, 100, 10, 5, None, fake,
+                             None, None, None) == EINVAL
+    assert lib.shouji_filter(None, None, None, None, 100, 0, 5, None, None, None, None, None) == OK
+    # compact: short or misaligned workspace, too many pairs, nulls
+    assert lib.shouji_compact(fake, 1000, fake, fake, fake, 0, None) == EINVAL
+    assert lib.shouji_compact(fake, 1000, fake, fake, ctypes.c_void_p(0x1008), 1 << 20, None) == EINVAL
+    assert lib.shouji_compact(fake, 1 << 32, fake, fake, fake, 1 << 30, None) == EINVAL
+    assert lib.shouji_compact(None, 1000, fake, fake, fake, 1 << 20, None) == EINVAL

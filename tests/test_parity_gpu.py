@@ -1,0 +1,247 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Integer work: the bar is bit-exact equality of the packed bases, the accept
+masks, the per-pair counts, the Shouji bit-vectors and the survivor indices.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1809_07858_gb300 as sj
+from paper_1809_07858_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CODE = {ord("A"): 0, ord("C"): 1, ord("G"): 3, ord("T"): 2, ord("N"): 3}
+
+
+# ---------------------------------------------------------------- helpers
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def unpack_planes(words, n, m):
+    """(n, m) 2-bit codes from the packed layout of include/shouji.h."""
+    tiles = (n + 1023) // 1024
+    w = words[: tiles * m * 64].view(np.uint32).reshape(tiles, m, 32, 2)
+    b = np.arange(32, dtype=np.uint32)
+    hi = (w[..., 0][..., None] >> b) & 1          # (tiles, m, lane, bit)
+    lo = (w[..., 1][..., None] >> b) & 1
+    codes = (hi * 2 + lo).transpose(0, 2, 3, 1).reshape(tiles * 1024, m)
+    return codes[:n].astype(np.uint8)
+
+
+def unpack_sliced(words, n, m):
+    """(n, m) bits from a one-plane bit-sliced array (N mask / Shouji vectors)."""
+    tiles = (n + 1023) // 1024
+    w = words[: tiles * m * 32].view(np.uint32).reshape(tiles, m, 32)
+    b = np.arange(32, dtype=np.uint32)
+    bits = (w[..., None] >> b) & 1
+    return bits.transpose(0, 2, 3, 1).reshape(tiles * 1024, m)[:n].astype(np.uint8)
+
+
+def accept_bits(acc_words, n):
+    w = acc_words.view(np.uint32)
+    return ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1)[:n].astype(bool)
+
+
+def gpu_filter(reads, refs, E, *, with_n=None, E_per_pair=None, vectors=False, stream=None):
+    n, m = reads.shape
+    if with_n is None:
+        with_n = bool((reads == 78).any() or (refs == 78).any())
+    r, t = to_dev(reads), to_dev(refs)
+    pr, nr = sj.shouji_pack(r, m, with_n=with_n, stream=stream)
+    pt, nt = sj.shouji_pack(t, m, with_n=with_n, stream=stream)
+    ep = to_dev(E_per_pair.astype(np.uint8)) if E_per_pair is not None else None
+    acc, cnt, vec = sj.shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
+                                     E_per_pair=ep, vectors=vectors, stream=stream)
+    torch.cuda.synchronize()
+    out = (accept_bits(acc.cpu().numpy(), n), cnt[:n].cpu().numpy())
+    if vectors:
+        out = out + (unpack_sliced(vec.cpu().numpy(), n, m),)
+    return out
+
+
+def adversarial(n, m, seed):
+    """Pairs that make ties: poly-A, short periods, identical, all-N, disjoint."""
+    rng = np.random.default_rng(seed)
+    pats = [b"A", b"AC", b"ACG", b"ACGT", b"AAC", b"ACGTT"]
+    reads = np.empty((n, m), np.uint8)
+    refs = np.empty((n, m), np.uint8)
+    for i in range(n):
+        kind = i % 8
+        if kind < 6:
+            p = np.frombuffer(pats[kind], np.uint8)
+            base = np.resize(p, m + 8)
+            off = rng.integers(0, 4)
+            reads[i] = base[:m]
+            refs[i] = base[off:off + m]
+            k = rng.integers(0, 4)
+            for _ in range(k):
+                refs[i, rng.integers(0, m)] = rng.choice(np.frombuffer(b"ACGT", np.uint8))
+        elif kind == 6:
+            reads[i] = ord("N")
+            refs[i] = rng.choice(np.frombuffer(b"ACGTN", np.uint8), m)
+        else:
+            reads[i] = rng.choice(np.frombuffer(b"AC", np.uint8), m)
+            refs[i] = rng.choice(np.frombuffer(b"GT", np.uint8), m)
+    return reads, refs
+
+
+def mixed_pairs(n, m, E, seed):
+    far = max(E + 1, m // 4)
+    r, t = synth.pairs(n, m, seed=seed, near=(0, max(E, 1)), far=(E + 1, far), far_fraction=0.5)
+    ar, at = adversarial(n // 8 + 1, m, seed + 1)
+    return np.concatenate([r, ar]), np.concatenate([t, at])
+
+
+def check_against_oracle(reads, refs, E, E_per_pair=None, vectors=False):
+    acc_o, cnt_o = oracle.shouji_batch(reads, refs, E, E_per_pair=E_per_pair, threads=8)
+    got = gpu_filter(reads, refs, E, E_per_pair=E_per_pair, vectors=vectors)
+    assert (got[1] == cnt_o).all(), "counts differ at %s" % np.flatnonzero(got[1] != cnt_o)[:10]
+    assert (got[0] == acc_o).all(), "accept differs at %s" % np.flatnonzero(got[0] != acc_o)[:10]
+    if vectors:
+        vec = got[2]
+        for i in range(0, len(reads), max(1, len(reads) // 300)):
+            e = int(E_per_pair[i]) if E_per_pair is not None else E
+            S, ones, _ = oracle.shouji(reads[i], refs[i], e)
+            assert (vec[i] == S).all(), "Shouji vector differs for pair %d" % i
+    return got
+
+
+# ---------------------------------------------------------------- pack
+@pytest.mark.parametrize("m", [1, 3, 4, 5, 33, 100, 150, 250, 255])
+@pytest.mark.parametrize("pad", [0, 13])
+def test_pack_layout(m, pad):
+    rng = np.random.default_rng(m * 7 + pad)
+    n = 2500
+    seqs = rng.choice(np.frombuffer(b"ACGTN", np.uint8), size=(n, m + pad))
+    d = to_dev(seqs)
+    packed, nmask = sj.shouji_pack(d, m, n=n, stride=m + pad, with_n=True)
+    torch.cuda.synchronize()
+    codes = unpack_planes(packed.cpu().numpy(), n, m)
+    want = np.vectorize(CODE.get)(seqs[:, :m]).astype(np.uint8)
+    assert (codes == want).all()
+    nb = unpack_sliced(nmask.cpu().numpy(), n, m)
+    assert (nb == (seqs[:, :m] == ord("N"))).all()
+    # sequences past n in the last tile are zeros
+    tiles = (n + 1023) // 1024
+    full = unpack_planes(packed.cpu().numpy(), tiles * 1024, m)
+    assert (full[n:] == 0).all()
+
+
+def test_pack_without_mask_reads_N_as_G():
+    seqs = np.frombuffer(b"ACGTN" * 20, np.uint8).reshape(1, 100).repeat(40, 0)
+    packed, nm = sj.shouji_pack(to_dev(seqs), 100)
+    torch.cuda.synchronize()
+    assert nm is None
+    assert (unpack_planes(packed.cpu().numpy(), 40, 100)[0, 4] == CODE[ord("G")])
+
+
+# ---------------------------------------------------------------- filter
+def test_small_workload_bit_exact():
+    """10,000 pairs, m=100, E=5 (the small synthetic workload), with vectors."""
+    reads, refs = synth.workload("small")
+    check_against_oracle(reads, refs, 5, vectors=True)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 7, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129,
+                               150, 250, 255])
+def test_lengths_bit_exact(m):
+    for E in sorted({0, 1, 2, 5, min(m + 1, 31)}):
+        reads, refs = mixed_pairs(1100, m, E, seed=100 + m + E)
+        check_against_oracle(reads, refs, E, vectors=(E == 5))
+
+
+@pytest.mark.parametrize("E", list(range(0, 32)))
+def test_every_threshold_bit_exact(E):
+    reads, refs = mixed_pairs(2100, 100, E, seed=300 + E)
+    check_against_oracle(reads, refs, E)
+
+
+@pytest.mark.parametrize("m,E", [(150, 7), (150, 15), (250, 12), (250, 15), (100, 5)])
+def test_N_masks_bit_exact(m, E):
+    """Long-read workload shape: 0.1% 'N' on each side, plus all-N pairs."""
+    reads, refs = synth.workload("long", 3000, m=m if m != 100 else 150, E=E)
+    if m == 100:
+        reads, refs = reads[:, :100].copy(), refs[:, :100].copy()
+    ar, at = adversarial(300, reads.shape[1], 7)
+    reads, refs = np.concatenate([reads, ar]), np.concatenate([refs, at])
+    assert (reads == ord("N")).any()
+    check_against_oracle(reads, refs, E, vectors=True)
+
+
+@pytest.mark.parametrize("Emax", [3, 12, 31])
+def test_per_pair_thresholds_bit_exact(Emax):
+    rng = np.random.default_rng(Emax)
+    reads, refs = mixed_pairs(3000, 150, Emax // 2, seed=500 + Emax)
+    Ep = rng.integers(0, Emax + 1, size=len(reads)).astype(np.uint8)
+    check_against_oracle(reads, refs, Emax, E_per_pair=Ep, vectors=True)
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 1023, 1024, 1025, 4097])
+def test_ragged_batch_sizes(n):
+    reads, refs = synth.workload("sweep", n, E=5)
+    check_against_oracle(reads, refs, 5)
+
+
+def test_identical_pairs_all_zero_vectors():
+    reads, _ = synth.workload("small", 1500)
+    acc, cnt, vec = gpu_filter(reads, reads, 5, vectors=True)
+    assert acc.all() and (cnt == 0).all() and (vec == 0).all()
+
+
+def test_nonzero_stream_and_zero_pairs():
+    reads, refs = synth.workload("small", 2000)
+    s = torch.cuda.Stream(device=dev())
+    with torch.cuda.stream(s):
+        got = gpu_filter(reads, refs, 5, stream=s)
+    base = gpu_filter(reads, refs, 5)
+    assert (got[0] == base[0]).all() and (got[1] == base[1]).all()
+    d = to_dev(reads)
+    pr, _ = sj.shouji_pack(d, 100)
+    sj.shouji_filter(pr, pr, 100, 0, 5)            # n = 0 is a no-op
+    idx, n = sj.shouji_compact(torch.zeros(1, dtype=torch.int32, device=dev()), 0)
+    torch.cuda.synchronize()
+    assert int(n.item()) == 0
+
+
+# ---------------------------------------------------------------- compact
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 1000, 131072, 131073, 5_000_001])
+@pytest.mark.parametrize("density", [0.0, 0.03, 0.5, 1.0])
+def test_compact_matches_flatnonzero(n, density):
+    rng = np.random.default_rng(n)
+    bits = rng.random(n) < density
+    words = np.zeros((n + 31) // 32 * 32, np.uint8)
+    words[:n] = bits
+    packed = np.packbits(words.reshape(-1, 32)[:, ::-1], axis=1).view(">u4").astype(np.uint32).ravel()
+    # garbage past n must be ignored
+    if n % 32:
+        packed[-1] |= np.uint32(0xFFFFFFFF) << np.uint32(n % 32)
+    acc = to_dev(packed.view(np.int32))
+    idx, cnt = sj.shouji_compact(acc, n)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    want = np.flatnonzero(bits)
+    assert k == len(want)
+    assert (idx[:k].cpu().numpy().view(np.uint32) == want).all()
+
+
+def test_pack_filter_compact_end_to_end():
+    reads, refs = synth.workload("sweep", 50_000, E=5)
+    acc_o, cnt_o = oracle.shouji_batch(reads, refs, 5, threads=8)
+    r, t = to_dev(reads), to_dev(refs)
+    pr, _ = sj.shouji_pack(r, 100)
+    pt, _ = sj.shouji_pack(t, 100)
+    acc, cnt, _ = sj.shouji_filter(pr, pt, 100, len(reads), 5)
+    idx, n = sj.shouji_compact(acc, len(reads))
+    torch.cuda.synchronize()
+    k = int(n.item())
+    assert (idx[:k].cpu().numpy() == np.flatnonzero(acc_o)).all()
