@@ -1,0 +1,366 @@
+"""Benchmark: sequence pairs filtered per second by the Shouji hot path on GB300.
+
+Workload (synthetic, shaped like the paper's m=100 datasets): 30,000,000 pairs
+of length m = 100 at threshold E = 5, half near (k ~ U{0..5} edits) and half
+far (k ~ U{6..25}), ASCII reads and references resident in HBM (6 GB, larger
+than L2, so no flush is needed between steps).  One step is the whole hot path
+over the batch: shouji_pack (reads), shouji_pack (refs), shouji_filter,
+shouji_compact.  ``e2e`` runs the same batch through the host pipeline
+(shouji_pipeline_run: pinned host buffers in, accept bits, counts and survivor
+indices out), with every copy inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank filters its own 30M pairs (weak scaling, no
+data exchange); rank 0 prints one JSON line.  ``--impl reference`` times the
+CPU oracle on the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sequence pairs filtered/sec on 1 GB300 at m=100,E=5 (bit-exact); % of roofline"
+UNIT = "pairs/s"
+N_PAIRS = 30_000_000
+M = 100
+E = 5
+ALU_LANES_PER_SM_CLK = 64   # LOP3/SHF/PRMT issue rate of the integer ALU pipe per SM
+# DRAM bytes per filter launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture, keyed by the hash of the filter kernel source it was
+# taken on; scaled to a 30M-pair launch.  Reported as null once the kernel
+# source changes.
+FILTER_TRAFFIC = {}
+
+
+def alu_ops_per_pair(m: int, E: int) -> float:
+    """Algorithmic integer lane-ops per pair of the bit-sliced formulation.
+
+    Per window and 32 pairs: map 2(2E+1), segment full adders 2(2E+1),
+    2E-1 candidate offers of 12 ops, the strict main-diagonal offer 18, the
+    Shouji-vector update 8 and the counter 4 -> 32E + 22 (E >= 1; 16 at E=0).
+    """
+    per_window = (32 * E + 22) if E >= 1 else 16
+    return m * per_window / 32.0
+
+
+def filter_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("shouji_filter.cuh",):
+        with open(os.path.join(ROOT, "paper_1809_07858_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.gpu_index = gpu_index
+        self.period_ms = period_ms
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def gpu_index_for(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def workload_config(n):
+    return {"workload": "sweep m=100 E=5: %d pairs, half near (k~U{0..5}) half far (k~U{6..25}), "
+                        "ASCII resident in HBM; step = pack reads + pack refs + filter + compact" % n,
+            "n_pairs": n, "m": M, "E": E,
+            "l2": "inputs larger than L2 (%.1f GB ASCII per step); no flush" % (2 * n * M / 1e9)}
+
+
+def cpu_oracle_rate(reads, refs, threads):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.shouji_batch(reads, refs, E, threads=threads)
+    return len(reads) / (time.perf_counter() - t0)
+
+
+def run_reference(args, world, rank):
+    """CPU oracle arm: each step filters a bounded sample on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401
+    from paper_1809_07858_gb300 import synth
+    sample = args.ref_sample
+    reads, refs = synth.workload("sweep", sample, E=E)
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_oracle_rate(reads, refs, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_rate(reads, refs, threads)
+    dt = time.perf_counter() - t0
+    value = sample * args.steps / dt
+    sample_desc = "pairs 0..%d of the sweep m=100 E=5 workload per step, %d threads" % (sample - 1, threads)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": dict(workload_config(sample), sample=sample_desc),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1809_07858_gb300 as sj
+    from paper_1809_07858_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.n
+
+    # Inputs: this rank's shard of the workload, generated into pinned host
+    # memory (the e2e leg reads it from there), then made resident in HBM.
+    h_reads = torch.empty((n, M), dtype=torch.uint8, pin_memory=True)
+    h_refs = torch.empty((n, M), dtype=torch.uint8, pin_memory=True)
+    synth.workload("sweep", n, E=E, first=rank * n, out=(h_reads, h_refs))
+    d_reads = h_reads.to(dev)
+    d_refs = h_refs.to(dev)
+    packed_r = torch.empty(sj.shouji_packed_words(n, M), dtype=torch.int32, device=dev)
+    packed_t = torch.empty_like(packed_r)
+    accept = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    count = torch.empty(n, dtype=torch.uint8, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    n_acc = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(max(16, sj.shouji_compact_workspace_size(n)), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ev = {k: [] for k in ("pack0", "pack1", "filter0", "filter1", "compact0", "compact1")}
+
+    def step(timed):
+        def mark(k):
+            if timed:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                ev[k].append(e)
+        mark("pack0")
+        sj.shouji_pack(d_reads, M, packed=packed_r, stream=stream)
+        sj.shouji_pack(d_refs, M, packed=packed_t, stream=stream)
+        mark("pack1")
+        mark("filter0")
+        sj.shouji_filter(packed_r, packed_t, M, n, E, out_accept=accept, out_count=count,
+                         stream=stream)
+        mark("filter1")
+        mark("compact0")
+        sj.shouji_compact(accept, n, out_idx=idx, out_n=n_acc, workspace=ws, stream=stream)
+        mark("compact1")
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(gpu_index_for(local)) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    def avg(a, b):
+        return sum(x.elapsed_time(y) for x, y in zip(ev[a], ev[b])) / max(1, len(ev[a]))
+
+    pack_ms, filter_ms, compact_ms = avg("pack0", "pack1"), avg("filter0", "filter1"), avg("compact0", "compact1")
+    n_accepted = int(n_acc.item())
+
+    # End to end through the host pipeline: pinned host ASCII in, accept words,
+    # counts and survivor indices out, every copy inside the timed region.
+    pipe = sj.Pipeline(M, chunk_pairs=args.chunk, max_pairs=n)
+    h_acc = torch.empty((n + 31) // 32, dtype=torch.int32, pin_memory=True)
+    h_cnt = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    h_idx = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    for _ in range(2):
+        pipe.run(h_reads, h_refs, n, E, h_acc, count=h_cnt, idx=h_idx)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_acc = pipe.run(h_reads, h_refs, n, E, h_acc, count=h_cnt, idx=h_idx)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    pipe.close()
+    assert e2e_acc == n_accepted, (e2e_acc, n_accepted)
+
+    if rank != 0:
+        return 0
+
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    peak_ops = sms * ALU_LANES_PER_SM_CLK * sm_max * 1e6
+    ops_launch = alu_ops_per_pair(M, E) * n
+    achieved = ops_launch / (filter_ms * 1e-3)
+    src = filter_source_hash()
+    traffic = FILTER_TRAFFIC.get(src)
+    value = world * n * args.steps / (elapsed_ms * 1e-3)
+    e2e_value = world * n * args.e2e_steps / e2e_s
+    h2d = 2 * n * M
+    d2h = h_acc.numel() * 4 + n + 4 * n_accepted
+    cpu = None
+    if world == 1:
+        sample = args.cpu_sample
+        threads = os.cpu_count() or 1
+        rate = cpu_oracle_rate(h_reads[:sample].numpy(), h_refs[:sample].numpy(), threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "pairs 0..%d of the same workload (%d threads)" % (sample - 1, threads)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": dict(workload_config(n), parallelism="independent shards" if world > 1 else "1 GPU"),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                "path": "shouji_pipeline_run, pinned host buffers, chunks of %d pairs" % args.chunk},
+        "gpu_launches": 6 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "lane-ops/s",
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "kernel": "shouji_filter", "ops_per_pair": alu_ops_per_pair(M, E),
+                     "peak_basis": "%d SMs x %d lane-ops/clk x %.0f MHz (max SM clock)" % (
+                         sms, ALU_LANES_PER_SM_CLK, sm_max),
+                     "filter_src": src},
+        "kernels_ms": {"pack_x2": pack_ms, "filter": filter_ms, "compact": compact_ms},
+        "accepted": n_accepted,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_PAIRS)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--chunk", type=int, default=1 << 22)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--ref-sample", type=int, default=200_000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -175,6 +175,55 @@ shouji_status shouji_compact(const uint32_t *accept, size_t n_pairs,
                              void *workspace, size_t workspace_bytes,
                              void *stream);
 
+/*
+ * Host pipeline -- the whole filter for pairs held in HOST memory.
+ *
+ * The paper's accelerator receives pairs from the host and returns one
+ * result bit per pair in input order (Sec. 2.3); this object does the same
+ * on a GPU: it cuts a batch into chunks and alternates two CUDA streams so
+ * that the host-to-device copy of one chunk overlaps the pack, filter and
+ * compaction of the previous one.
+ *
+ * shouji_pipeline_create allocates every device buffer the runs need on the
+ * current device (two chunk slots, an index array for max_pairs survivors)
+ * and the two streams.
+ *   m            sequence length, 1 <= m <= SHOUJI_MAX_M.
+ *   chunk_pairs  pairs per chunk (> 0; rounded up to a multiple of 1024).
+ *   max_pairs    largest n_pairs whose survivor indices a run may return
+ *                (< 2^32; 0 = runs return no indices).
+ *   with_n       nonzero: 'N' bases match nothing (N masks are built).
+ *   out          receives the pipeline; NULL on failure.
+ * Errors: SHOUJI_EINVAL, SHOUJI_ENOMEM (nothing is leaked), SHOUJI_ECUDA.
+ *
+ * shouji_pipeline_run filters n_pairs pairs and returns when all results
+ * are in host memory (it synchronizes its own streams only).  Host buffers
+ * should be pinned (cudaHostAlloc) for the copies to overlap.
+ *   reads, refs  host, n_pairs rows of m bytes, row i at + i * stride.
+ *   E            0 <= E <= SHOUJI_MAX_E.
+ *   accept       host uint32[ceil(n_pairs / 32)] (layout of shouji_filter).
+ *   count        host uint8[n_pairs] or NULL.
+ *   idx          host uint32[n_pairs] or NULL: survivor indices, in order
+ *                (needs n_pairs <= max_pairs).
+ *   n_accepted   host, or NULL: number of accepted pairs.
+ * Errors: SHOUJI_EINVAL (bad argument, nothing launched), SHOUJI_ECUDA.
+ *
+ * shouji_pipeline_destroy frees everything (NULL is a no-op).  A pipeline
+ * must not be used by two host threads at once.
+ */
+typedef struct shouji_pipeline shouji_pipeline;
+
+shouji_status shouji_pipeline_create(uint32_t m, size_t chunk_pairs,
+                                     size_t max_pairs, int with_n,
+                                     shouji_pipeline **out);
+
+shouji_status shouji_pipeline_run(shouji_pipeline *pipeline,
+                                  const uint8_t *reads, const uint8_t *refs,
+                                  uint64_t stride, size_t n_pairs, int E,
+                                  uint32_t *accept, uint8_t *count,
+                                  uint32_t *idx, uint64_t *n_accepted);
+
+void shouji_pipeline_destroy(shouji_pipeline *pipeline);
+
 #ifdef __cplusplus
 }
 #endif

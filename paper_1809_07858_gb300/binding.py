@@ -23,7 +23,7 @@ __all__ = [
     "load_library", "shouji_status_string", "shouji_last_cuda_error",
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
-    "accept_to_bool",
+    "accept_to_bool", "Pipeline",
 ]
 
 _lib = None
@@ -63,6 +63,13 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_compact_workspace_size.restype = sz
     lib.shouji_compact.argtypes = [vp, sz, vp, vp, vp, sz, vp]
     lib.shouji_compact.restype = ctypes.c_int
+    lib.shouji_pipeline_create.argtypes = [u32, sz, sz, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.shouji_pipeline_create.restype = ctypes.c_int
+    lib.shouji_pipeline_run.argtypes = [vp, vp, vp, u64, sz, ctypes.c_int, vp, vp, vp,
+                                        ctypes.POINTER(ctypes.c_uint64)]
+    lib.shouji_pipeline_run.restype = ctypes.c_int
+    lib.shouji_pipeline_destroy.argtypes = [vp]
+    lib.shouji_pipeline_destroy.restype = None
     _lib = lib
     return lib
 
@@ -207,3 +214,52 @@ def filter_pairs(reads, refs, E: int, *, with_n: bool | None = None, E_per_pair=
     acc, cnt, _ = shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
                                 E_per_pair=E_per_pair, stream=stream)
     return accept_to_bool(acc, n), cnt[:n]
+
+
+def _host_ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert not a.is_cuda and a.is_contiguous()
+        return a.data_ptr()
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+class Pipeline:
+    """``shouji_pipeline_*``: the whole filter for pairs held in host memory.
+
+    Buffers are numpy arrays or CPU torch tensors (pin them for overlap).
+    """
+
+    def __init__(self, m: int, chunk_pairs: int = 1 << 22, max_pairs: int = 0,
+                 with_n: bool = False):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.shouji_pipeline_create(m, chunk_pairs, max_pairs, int(with_n),
+                                          ctypes.byref(h)), "shouji_pipeline_create")
+        self._h = h
+        self.m = m
+        self.max_pairs = max_pairs
+
+    def run(self, reads, refs, n_pairs: int, E: int, accept, *, count=None, idx=None,
+            stride: int | None = None) -> int:
+        """Filter; fills ``accept`` (uint32[ceil(n/32)]) and optionally
+        ``count`` and ``idx``; returns the number of accepted pairs."""
+        n_acc = ctypes.c_uint64(0)
+        _check(load_library().shouji_pipeline_run(
+            self._h, _host_ptr(reads), _host_ptr(refs), self.m if stride is None else stride,
+            n_pairs, E, _host_ptr(accept), _host_ptr(count), _host_ptr(idx),
+            ctypes.byref(n_acc)), "shouji_pipeline_run")
+        return n_acc.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().shouji_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -80,10 +80,14 @@ compact_count(const uint32_t *__restrict__ accept, size_t n_pairs, size_t n_word
         slice_sums[blockIdx.x] = total;
 }
 
+// accumulate = 0: *out_n = total.  accumulate = 1: the offsets start at the
+// value already in *out_n and *out_n grows by the total (chunked runs).
 __global__ void __launch_bounds__(kCThreads)
-compact_scan(uint32_t *__restrict__ slice_sums, uint32_t n_slices, uint32_t *__restrict__ out_n)
+compact_scan(uint32_t *__restrict__ slice_sums, uint32_t n_slices, uint32_t *__restrict__ out_n,
+             int accumulate)
 {
-    uint32_t carry = 0;
+    uint32_t carry = accumulate ? *out_n : 0u;
+    __syncthreads();
     for (uint32_t base = 0; base < n_slices; base += kCThreads) {
         const uint32_t i = base + threadIdx.x;
         const uint32_t x = i < n_slices ? slice_sums[i] : 0u;
@@ -99,7 +103,8 @@ compact_scan(uint32_t *__restrict__ slice_sums, uint32_t n_slices, uint32_t *__r
 
 __global__ void __launch_bounds__(kCThreads)
 compact_write(const uint32_t *__restrict__ accept, size_t n_pairs, size_t n_words,
-              const uint32_t *__restrict__ slice_offsets, uint32_t *__restrict__ out_idx)
+              const uint32_t *__restrict__ slice_offsets, uint32_t *__restrict__ out_idx,
+              uint32_t pair_base)
 {
     // Thread t owns words w0 + t*16 .. w0 + t*16 + 15 (consecutive), so the
     // order of threads is the order of pairs.
@@ -117,7 +122,7 @@ compact_write(const uint32_t *__restrict__ accept, size_t n_pairs, size_t n_word
 #pragma unroll
     for (int i = 0; i < kWordsPerThread; ++i) {
         uint32_t w = words[i];
-        const uint32_t pair0 = (uint32_t)((w0 + i) * 32);
+        const uint32_t pair0 = pair_base + (uint32_t)((w0 + i) * 32);
         while (w) {
             const int b = __ffs(w) - 1;
             out_idx[pos++] = pair0 + (uint32_t)b;
@@ -138,12 +143,20 @@ size_t compact_workspace_bytes(size_t n_pairs)
 cudaError_t launch_compact(const uint32_t *accept, size_t n_pairs, uint32_t *out_idx,
                            uint32_t *out_n, void *workspace, cudaStream_t s)
 {
+    return launch_compact_append(accept, n_pairs, 0u, out_idx, out_n, 0, workspace, s);
+}
+
+cudaError_t launch_compact_append(const uint32_t *accept, size_t n_pairs, uint32_t pair_base,
+                                  uint32_t *out_idx, uint32_t *total, int accumulate,
+                                  void *workspace, cudaStream_t s)
+{
     const size_t n_words = groups_of(n_pairs);
     const size_t slices = (n_words + kSliceWords - 1) / kSliceWords;
     uint32_t *sums = static_cast<uint32_t *>(workspace);
     compact_count<<<(unsigned)slices, kCThreads, 0, s>>>(accept, n_pairs, n_words, sums);
-    compact_scan<<<1, kCThreads, 0, s>>>(sums, (uint32_t)slices, out_n);
-    compact_write<<<(unsigned)slices, kCThreads, 0, s>>>(accept, n_pairs, n_words, sums, out_idx);
+    compact_scan<<<1, kCThreads, 0, s>>>(sums, (uint32_t)slices, total, accumulate);
+    compact_write<<<(unsigned)slices, kCThreads, 0, s>>>(accept, n_pairs, n_words, sums, out_idx,
+                                                         pair_base);
     return cudaGetLastError();
 }
 

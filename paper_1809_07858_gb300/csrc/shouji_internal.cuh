@@ -43,5 +43,11 @@ size_t compact_workspace_bytes(size_t n_pairs);
 cudaError_t launch_compact(const uint32_t *accept, size_t n_pairs,
                            uint32_t *out_idx, uint32_t *out_n, void *workspace,
                            cudaStream_t s);
+// Chunked form: indices are offset by pair_base; with accumulate the output
+// position starts at *total and *total grows by the chunk's count.
+cudaError_t launch_compact_append(const uint32_t *accept, size_t n_pairs,
+                                  uint32_t pair_base, uint32_t *out_idx,
+                                  uint32_t *total, int accumulate,
+                                  void *workspace, cudaStream_t s);
 
 }  // namespace shouji

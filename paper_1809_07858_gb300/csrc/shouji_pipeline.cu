@@ -1,0 +1,238 @@
+// Host pipeline: the whole filter for pairs held in host memory.
+//
+// The paper's accelerator streams pairs from the host over PCIe to its
+// filtering units and returns one bit per pair in input order (Sec. 2.3,
+// Sec. 3.3).  On a GB300 the link is NVLink-C2C to the Grace host; the
+// pipeline cuts the batch into chunks and alternates two CUDA streams, so the
+// host-to-device copy of one chunk overlaps the pack / filter / compaction of
+// the previous one:
+//   H2D reads, refs -> shouji_pack x2 -> shouji_filter -> D2H accept (+count)
+//                                                     -> compaction (+indices)
+// Survivor indices of successive chunks are appended to one device array in
+// input order (the compaction of chunk k waits for that of chunk k-1 through
+// an event, and carries the running total on the device), and copied back
+// once at the end.  All device memory is allocated by shouji_pipeline_create.
+#include <stdlib.h>
+#include <string.h>
+
+#include "shouji_internal.cuh"
+
+struct shouji_pipeline {
+    int device;
+    uint32_t m;
+    size_t chunk;      // pairs per chunk, multiple of 1024
+    size_t max_pairs;  // capacity of the survivor index array
+    int with_n;
+    cudaStream_t st[2];
+    cudaEvent_t ev_compact;
+    uint8_t *d_reads[2], *d_refs[2];
+    uint32_t *d_pr[2], *d_pt[2], *d_nr[2], *d_nt[2];
+    uint32_t *d_acc[2];
+    uint8_t *d_cnt[2];
+    void *d_ws[2];
+    uint32_t *d_idx;
+    uint32_t *d_total;
+    uint32_t *h_total;  // pinned
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        if (prev != dev)
+            cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+void release(shouji_pipeline *p)
+{
+    if (!p)
+        return;
+    DeviceGuard g(p->device);
+    for (int s = 0; s < 2; ++s) {
+        cudaFree(p->d_reads[s]);
+        cudaFree(p->d_refs[s]);
+        cudaFree(p->d_pr[s]);
+        cudaFree(p->d_pt[s]);
+        cudaFree(p->d_nr[s]);
+        cudaFree(p->d_nt[s]);
+        cudaFree(p->d_acc[s]);
+        cudaFree(p->d_cnt[s]);
+        cudaFree(p->d_ws[s]);
+        if (p->st[s])
+            cudaStreamDestroy(p->st[s]);
+    }
+    cudaFree(p->d_idx);
+    cudaFree(p->d_total);
+    if (p->h_total)
+        cudaFreeHost(p->h_total);
+    if (p->ev_compact)
+        cudaEventDestroy(p->ev_compact);
+    free(p);
+}
+
+}  // namespace
+
+using namespace shouji;
+
+extern "C" {
+
+shouji_status shouji_pipeline_create(uint32_t m, size_t chunk_pairs, size_t max_pairs,
+                                     int with_n, shouji_pipeline **out)
+{
+    if (!out || m < 1 || m > SHOUJI_MAX_M || chunk_pairs == 0 ||
+        max_pairs >= ((size_t)1 << 32))
+        return SHOUJI_EINVAL;
+    *out = nullptr;
+    shouji_pipeline *p = (shouji_pipeline *)calloc(1, sizeof(shouji_pipeline));
+    if (!p)
+        return SHOUJI_ENOMEM;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        free(p);
+        return cuda_status(e);
+    }
+    p->m = m;
+    p->chunk = (chunk_pairs + kTile - 1) / kTile * kTile;
+    p->max_pairs = max_pairs;
+    p->with_n = with_n ? 1 : 0;
+    const size_t ascii = p->chunk * m;
+    const size_t packed = shouji_packed_words(p->chunk, m) * 4;
+    const size_t nmask = shouji_nmask_words(p->chunk, m) * 4;
+    const size_t words = groups_of(p->chunk) * 4;
+    const size_t ws = compact_workspace_bytes(p->chunk);
+    bool ok = true;
+    for (int s = 0; s < 2 && ok; ++s) {
+        ok = ok && cudaStreamCreateWithFlags(&p->st[s], cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaMalloc(&p->d_reads[s], ascii) == cudaSuccess;
+        ok = ok && cudaMalloc(&p->d_refs[s], ascii) == cudaSuccess;
+        ok = ok && cudaMalloc(&p->d_pr[s], packed) == cudaSuccess;
+        ok = ok && cudaMalloc(&p->d_pt[s], packed) == cudaSuccess;
+        if (p->with_n) {
+            ok = ok && cudaMalloc(&p->d_nr[s], nmask) == cudaSuccess;
+            ok = ok && cudaMalloc(&p->d_nt[s], nmask) == cudaSuccess;
+        }
+        ok = ok && cudaMalloc(&p->d_acc[s], words) == cudaSuccess;
+        ok = ok && cudaMalloc(&p->d_cnt[s], p->chunk) == cudaSuccess;
+        ok = ok && cudaMalloc(&p->d_ws[s], ws) == cudaSuccess;
+    }
+    if (ok && max_pairs)
+        ok = cudaMalloc(&p->d_idx, max_pairs * sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->d_total, sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&p->h_total, sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&p->ev_compact, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        release(p);
+        return SHOUJI_ENOMEM;
+    }
+    *out = p;
+    return SHOUJI_OK;
+}
+
+void shouji_pipeline_destroy(shouji_pipeline *p) { release(p); }
+
+shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, const uint8_t *refs,
+                                  uint64_t stride, size_t n_pairs, int E, uint32_t *accept,
+                                  uint8_t *count, uint32_t *idx, uint64_t *n_accepted)
+{
+    if (!p || E < 0 || E > SHOUJI_MAX_E || stride < p->m)
+        return SHOUJI_EINVAL;
+    if (n_pairs == 0) {
+        if (n_accepted)
+            *n_accepted = 0;
+        return SHOUJI_OK;
+    }
+    if (!reads || !refs || !accept)
+        return SHOUJI_EINVAL;
+    if (idx && n_pairs > p->max_pairs)
+        return SHOUJI_EINVAL;
+    DeviceGuard g(p->device);
+    const uint32_t m = p->m;
+    const bool want_idx = idx != nullptr;
+    cudaError_t e = cudaSuccess;
+#define SHOUJI_TRY(x)                          \
+    do {                                       \
+        e = (x);                               \
+        if (e != cudaSuccess)                  \
+            return cuda_status(e);             \
+    } while (0)
+    if (want_idx) {
+        SHOUJI_TRY(cudaMemsetAsync(p->d_total, 0, sizeof(uint32_t), p->st[0]));
+        SHOUJI_TRY(cudaEventRecord(p->ev_compact, p->st[0]));
+    }
+    int slot = 0;
+    for (size_t base = 0; base < n_pairs; base += p->chunk, slot ^= 1) {
+        cudaStream_t s = p->st[slot];
+        const size_t nc = (n_pairs - base < p->chunk) ? n_pairs - base : p->chunk;
+        if (stride == m) {
+            SHOUJI_TRY(cudaMemcpyAsync(p->d_reads[slot], reads + base * m, nc * m,
+                                       cudaMemcpyHostToDevice, s));
+            SHOUJI_TRY(cudaMemcpyAsync(p->d_refs[slot], refs + base * m, nc * m,
+                                       cudaMemcpyHostToDevice, s));
+        } else {
+            SHOUJI_TRY(cudaMemcpy2DAsync(p->d_reads[slot], m, reads + base * stride, stride, m,
+                                         nc, cudaMemcpyHostToDevice, s));
+            SHOUJI_TRY(cudaMemcpy2DAsync(p->d_refs[slot], m, refs + base * stride, stride, m,
+                                         nc, cudaMemcpyHostToDevice, s));
+        }
+        SHOUJI_TRY(launch_pack(p->d_reads[slot], m, nc, (int)m, p->d_pr[slot],
+                               p->with_n ? p->d_nr[slot] : nullptr, s));
+        SHOUJI_TRY(launch_pack(p->d_refs[slot], m, nc, (int)m, p->d_pt[slot],
+                               p->with_n ? p->d_nt[slot] : nullptr, s));
+        FilterArgs a;
+        a.reads = reinterpret_cast<const uint2 *>(p->d_pr[slot]);
+        a.refs = reinterpret_cast<const uint2 *>(p->d_pt[slot]);
+        a.reads_n = p->with_n ? p->d_nr[slot] : nullptr;
+        a.refs_n = p->with_n ? p->d_nt[slot] : nullptr;
+        a.E_per_pair = nullptr;
+        a.accept = p->d_acc[slot];
+        a.count = count ? p->d_cnt[slot] : nullptr;
+        a.vectors = nullptr;
+        a.n_pairs = nc;
+        a.m = (int)m;
+        SHOUJI_TRY(launch_filter(a, E, s));
+        SHOUJI_TRY(cudaMemcpyAsync(accept + base / 32, p->d_acc[slot], groups_of(nc) * 4,
+                                   cudaMemcpyDeviceToHost, s));
+        if (count)
+            SHOUJI_TRY(cudaMemcpyAsync(count + base, p->d_cnt[slot], nc, cudaMemcpyDeviceToHost, s));
+        if (want_idx) {
+            SHOUJI_TRY(cudaStreamWaitEvent(s, p->ev_compact, 0));
+            SHOUJI_TRY(launch_compact_append(p->d_acc[slot], nc, (uint32_t)base, p->d_idx,
+                                             p->d_total, 1, p->d_ws[slot], s));
+            SHOUJI_TRY(cudaEventRecord(p->ev_compact, s));
+        }
+    }
+    SHOUJI_TRY(cudaStreamSynchronize(p->st[0]));
+    SHOUJI_TRY(cudaStreamSynchronize(p->st[1]));
+    uint64_t total = 0;
+    if (want_idx) {
+        SHOUJI_TRY(cudaMemcpyAsync(p->h_total, p->d_total, sizeof(uint32_t),
+                                   cudaMemcpyDeviceToHost, p->st[0]));
+        SHOUJI_TRY(cudaStreamSynchronize(p->st[0]));
+        total = *p->h_total;
+        if (total)
+            SHOUJI_TRY(cudaMemcpyAsync(idx, p->d_idx, total * sizeof(uint32_t),
+                                       cudaMemcpyDeviceToHost, p->st[0]));
+        SHOUJI_TRY(cudaStreamSynchronize(p->st[0]));
+    } else if (n_accepted) {
+        const size_t words = groups_of(n_pairs);
+        for (size_t w = 0; w < words; ++w)
+            total += (uint64_t)__builtin_popcount(accept[w]);
+    }
+#undef SHOUJI_TRY
+    if (n_accepted)
+        *n_accepted = total;
+    return SHOUJI_OK;
+}
+
+}  // extern "C"

@@ -245,3 +245,37 @@ def test_pack_filter_compact_end_to_end():
     torch.cuda.synchronize()
     k = int(n.item())
     assert (idx[:k].cpu().numpy() == np.flatnonzero(acc_o)).all()
+
+
+# ---------------------------------------------------------------- host pipeline
+@pytest.mark.parametrize("n,chunk", [(1, 1024), (5000, 1024), (70_001, 16384)])
+def test_host_pipeline_bit_exact(n, chunk):
+    dev()
+    reads, refs = synth.workload("sweep", n, E=5)
+    acc_o, cnt_o = oracle.shouji_batch(reads, refs, 5, threads=8)
+    pipe = sj.Pipeline(100, chunk_pairs=chunk, max_pairs=n)
+    acc = np.zeros((n + 31) // 32, np.uint32)
+    cnt = np.zeros(n, np.uint8)
+    idx = np.zeros(n, np.uint32)
+    k = pipe.run(reads, refs, n, 5, acc, count=cnt, idx=idx)
+    pipe.close()
+    assert k == int(acc_o.sum())
+    assert (accept_bits(acc.view(np.int32), n) == acc_o).all()
+    assert (cnt == cnt_o).all()
+    assert (idx[:k] == np.flatnonzero(acc_o)).all()
+
+
+def test_host_pipeline_strided_rows_with_N():
+    dev()
+    n, m, E = 9000, 150, 7
+    reads, refs = synth.workload("long", n, m=m, E=E)
+    acc_o, cnt_o = oracle.shouji_batch(reads, refs, E, threads=8)
+    pr = np.zeros((n, 160), np.uint8)
+    pt = np.zeros((n, 160), np.uint8)
+    pr[:, :m], pt[:, :m] = reads, refs
+    pipe = sj.Pipeline(m, chunk_pairs=4096, max_pairs=0, with_n=True)
+    acc = np.zeros((n + 31) // 32, np.uint32)
+    k = pipe.run(pr, pt, n, E, acc, stride=160)
+    pipe.close()
+    assert k == int(acc_o.sum())
+    assert (accept_bits(acc.view(np.int32), n) == acc_o).all()
