@@ -33,6 +33,9 @@ namespace shouji {
 namespace filt {
 
 constexpr int kThreads = 128;
+#ifndef SHOUJI_FILTER_U
+#define SHOUJI_FILTER_U 4
+#endif
 
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c)
 {
@@ -80,24 +83,28 @@ __device__ __forceinline__ void offer(Pick &b, uint32_t a0, uint32_t a1, uint32_
 }
 
 // The main diagonal replaces the choice only with strictly more zeros:
-// ones(z) > ones(main).
+// ones(z) > ones(main) <=> ones(z) + ones(~main) >= 5, with
+// ones(~main) = ~m0 + ~ms + 2 ~mc (ms, mc: full adder of main bits 1..3).
+// Summing z0 + ~m0 + zs -> (f0, f1), f0 + ~ms -> (g0, g1), g1 + f1 + zc ->
+// (k0, k1): total = g0 + 2 h with h = k0 + 2 k1 + ~mc, and total >= 5 <=>
+// h >= 3 or (h >= 2 and g0).
 __device__ __forceinline__ void offer_main(Pick &b, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3)
 {
-    const uint32_t as = a1 ^ a2 ^ a3;
-    const uint32_t ac = maj3(a1, a2, a3);
-    // 3-bit popcounts: ones(z) = (p2 p1 p0), ones(main) = (q2 q1 q0)
-    const uint32_t p0 = b.z0 ^ b.zs, pk = b.z0 & b.zs;
-    const uint32_t p1 = b.zc ^ pk, p2 = b.zc & pk;
-    const uint32_t q0 = a0 ^ as, qk = a0 & as;
-    const uint32_t q1 = ac ^ qk, q2 = ac & qk;
-    const uint32_t gt = (p2 & ~q2) |
-                        (~(p2 ^ q2) & ((p1 & ~q1) | (~(p1 ^ q1) & p0 & ~q0)));
+    const uint32_t ms = a1 ^ a2 ^ a3;
+    const uint32_t mc = maj3(a1, a2, a3);
+    const uint32_t f0 = b.z0 ^ ~a0 ^ b.zs;
+    const uint32_t f1 = maj3(b.z0, ~a0, b.zs);
+    const uint32_t g0 = f0 ^ ~ms;
+    const uint32_t g1 = f0 & ~ms;
+    const uint32_t k0 = g1 ^ f1 ^ b.zc;
+    const uint32_t k1 = maj3(g1, f1, b.zc);
+    const uint32_t gt = (k1 & (k0 | ~mc)) | (g0 & (k1 | (k0 & ~mc)));
     b.z0 = (gt & a0) | (~gt & b.z0);
     b.z1 = (gt & a1) | (~gt & b.z1);
     b.z2 = (gt & a2) | (~gt & b.z2);
     b.z3 = (gt & a3) | (~gt & b.z3);
-    b.zs = (gt & as) | (~gt & b.zs);
-    b.zc = (gt & ac) | (~gt & b.zc);
+    b.zs = (gt & ms) | (~gt & b.zs);
+    b.zc = (gt & mc) | (~gt & b.zc);
 }
 
 // Bit-sliced 8-bit counter += x (3-bit value x2 x1 x0).
@@ -119,6 +126,66 @@ __device__ __forceinline__ void counter_add3(uint32_t (&C)[8], uint32_t x0, uint
         C[i] ^= k;
         k = c;
     }
+}
+
+// 4x4 byte transpose: out[q] byte u = in[u] byte q.
+__device__ __forceinline__ void byte_transpose4(uint32_t y0, uint32_t y1, uint32_t y2, uint32_t y3,
+                                                uint32_t out[4])
+{
+    const uint32_t a = __byte_perm(y0, y1, 0x5140);
+    const uint32_t b = __byte_perm(y0, y1, 0x7362);
+    const uint32_t c = __byte_perm(y2, y3, 0x5140);
+    const uint32_t d = __byte_perm(y2, y3, 0x7362);
+    out[0] = __byte_perm(a, c, 0x5410);
+    out[1] = __byte_perm(a, c, 0x7632);
+    out[2] = __byte_perm(b, d, 0x5410);
+    out[3] = __byte_perm(b, d, 0x7632);
+}
+
+// Transpose of the 8x8 bit matrix held in a 64-bit word (bit 8r + c <->
+// bit 8c + r), by three rounds of masked swaps (Hacker's Delight, 7-3).
+__device__ __forceinline__ uint64_t bit_transpose8(uint64_t x)
+{
+    uint64_t t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+    x = x ^ t ^ (t << 7);
+    t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+    x = x ^ t ^ (t << 14);
+    t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+    x = x ^ t ^ (t << 28);
+    return x;
+}
+
+// Bit-sliced 8-bit counts (plane k, bit b = bit k of pair b's count) to one
+// byte per pair: cw[q] byte u = count of pair 4q + u.
+__device__ __forceinline__ void counts_to_bytes(const uint32_t (&C)[8], uint32_t (&cw)[8])
+{
+    uint32_t lo[4], hi[4];
+    byte_transpose4(C[0], C[1], C[2], C[3], lo);  // lo[j] byte k = byte j of C[k]
+    byte_transpose4(C[4], C[5], C[6], C[7], hi);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        // bit 8k + i = bit k of the count of pair 8j + i
+        const uint64_t x = bit_transpose8(((uint64_t)hi[j] << 32) | lo[j]);
+        cw[2 * j] = (uint32_t)x;
+        cw[2 * j + 1] = (uint32_t)(x >> 32);
+    }
+}
+
+// Accept bits for a constant threshold: bit b = (count of pair b) <= E.
+template <int E>
+__device__ __forceinline__ uint32_t le_const(const uint32_t (&C)[8])
+{
+    uint32_t gt = 0u, eq = ~0u;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        if ((E >> k) & 1) {
+            eq &= C[k];
+        } else {
+            gt |= eq & C[k];
+            eq &= ~C[k];
+        }
+    }
+    return ~gt;
 }
 
 // Per-thread view of the packed data of one group of 32 pairs.
@@ -310,27 +377,16 @@ filter_kernel(FilterArgs a)
     }
 
     // Per-pair counts and the accept word.
-    uint32_t acc = 0;
     uint32_t cw[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        uint32_t word = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int b = 4 * q + u;
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                cnt |= ((C[k] >> b) & 1u) << k;
-            uint32_t thr = (uint32_t)E;
-            if (MASKS && a.E_per_pair && (size_t)b < left) {
-                const uint32_t e = a.E_per_pair[first + b];
-                thr = e < thr ? e : thr;
-            }
-            acc |= (uint32_t)(cnt <= thr) << b;
-            word |= cnt << (8 * u);
+    counts_to_bytes(C, cw);
+    uint32_t acc = le_const<E>(C);
+    if (MASKS && a.E_per_pair) {
+        acc = 0u;
+        for (int b = 0; b < 32 && (size_t)b < left; ++b) {
+            const uint32_t cnt = (cw[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+            const uint32_t e = a.E_per_pair[first + b];
+            acc |= (uint32_t)(cnt <= e && cnt <= (uint32_t)E) << b;
         }
-        cw[q] = word;
     }
     if (left < 32)
         acc &= (1u << left) - 1u;
@@ -350,7 +406,7 @@ filter_kernel(FilterArgs a)
 template <int E>
 cudaError_t launch_E(const FilterArgs &a, cudaStream_t s)
 {
-    constexpr int U = 4;
+    constexpr int U = SHOUJI_FILTER_U;
     const size_t groups = groups_of(a.n_pairs);
     const size_t blocks = (groups + kThreads - 1) / kThreads;
     if (a.reads_n || a.E_per_pair)

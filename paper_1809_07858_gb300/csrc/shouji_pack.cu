@@ -7,14 +7,18 @@
 // ASCII byte: A=00, C=01, G=11, T=10 (hi, lo); 'N' is flagged separately.
 //
 // One CTA of 256 threads packs 256 sequences = 8 lanes of a 1024-sequence
-// tile.  Phase 1 stages the 256 rows in shared memory (rows padded to whole
-// words, 4 words of skew per 32 rows so that phase 2 is free of bank
-// conflicts).  Phase 2: a thread owns (lane, 4 consecutive positions); it
-// reads one word (4 bases) of each of the lane's 32 sequences, gathers bit 2
-// / bit 1 / is-'N' of every byte into byte-sliced words with shifts and
-// masks, and a 4x4 byte transpose (PRMT) turns them into the four output
-// words of each plane.  Stores are 32-byte (N mask) or 64-byte (planes)
-// contiguous segments.
+// tile.  Phase 1 copies the CTA's rows into shared memory as one dense block
+// (row r at byte r*m).  When the rows are contiguous in global memory
+// (stride == m) the block is a single contiguous range and is copied with
+// 16-byte (or 4-byte) loads, four in flight per thread; otherwise row by
+// row.  Phase 2: a thread owns (lane, 4 consecutive positions); it reads one
+// word (4 bases) of each of the lane's 32 sequences, gathers bit 2 / bit 1 /
+// is-'N' of every byte into byte-sliced words with shifts and masks, and a
+// 4x4 byte transpose (PRMT) turns them into the four output words of each
+// plane.  The 32 sequences are visited in an order rotated by a per-lane
+// offset so that the 32 threads of a warp hit 32 different banks; the
+// output word is rotated back.  Stores are 32-byte (N mask) or 64-byte
+// (planes) contiguous segments.
 #include "shouji_internal.cuh"
 
 namespace shouji {
@@ -22,8 +26,6 @@ namespace {
 
 constexpr int kPackThreads = 256;
 constexpr int kPackSeqs = 256;  // 8 lanes
-
-__device__ __forceinline__ int row_word(int r, int W) { return r * W + 4 * (r >> 5); }
 
 // 4x4 byte transpose: out[q] byte u = in[u] byte q.
 __device__ __forceinline__ void transpose4x4(uint32_t y0, uint32_t y1, uint32_t y2,
@@ -47,64 +49,92 @@ __device__ __forceinline__ uint32_t n_bytes(uint32_t w)
     return ~t & 0x80808080u;
 }
 
-template <bool WITH_N>
+enum CopyMode { kCopyVec16 = 0, kCopyVec4 = 1, kCopyRows = 2 };
+
+// ALIGNED: m % 4 == 0, so every 4-position word of a row is word-aligned.
+template <bool WITH_N, bool ALIGNED>
 __global__ void __launch_bounds__(kPackThreads)
 pack_kernel(const uint8_t *__restrict__ seqs, uint64_t stride, size_t n, int m,
-            uint32_t *__restrict__ packed, uint32_t *__restrict__ nmask, int word_rows)
+            uint32_t *__restrict__ packed, uint32_t *__restrict__ nmask, int copy_mode,
+            int rot_step)
 {
-    extern __shared__ uint32_t sm[];
-    const int W = (m + 3) >> 2;  // words per staged row
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint8_t *sb = reinterpret_cast<uint8_t *>(sm);
     const size_t seq0 = (size_t)blockIdx.x * kPackSeqs;
     const size_t tile = seq0 / kTile;
     const int lane0 = (int)((seq0 % kTile) / 32);
+    // Blocks of the last tile may start at or past n: they stage no rows.
+    const size_t left = seq0 < n ? n - seq0 : 0;
+    const int rows = (int)(left < (size_t)kPackSeqs ? left : (size_t)kPackSeqs);
+    const int nbytes = rows * m;                 // staged bytes holding real rows
+    const int total = kPackSeqs * m + 16;        // staged bytes incl. zero padding
+    const int tid = threadIdx.x;
 
-    // Phase 1: stage rows seq0 .. seq0+255 (zeros past n).
-    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    if (word_rows) {
-        // Whole words inside the row are loaded as words; a partial last word
-        // (m % 4 != 0) byte by byte, so nothing past byte m-1 is read.
-        const int Wfull = m >> 2;
-        for (int r = warp; r < kPackSeqs; r += kPackThreads / 32) {
-            uint32_t *dst = sm + row_word(r, W);
-            const size_t s = seq0 + r;
-            const uint32_t *src = (const uint32_t *)(seqs + s * stride);
-            for (int j = ln; j < W; j += 32) {
-                uint32_t x = 0u;
-                if (s < n) {
-                    if (j < Wfull) {
-                        x = __ldg(src + j);
-                    } else {
-                        const uint8_t *sb = (const uint8_t *)src;
-                        for (int k = 0; 4 * j + k < m; ++k)
-                            x |= (uint32_t)__ldg(sb + 4 * j + k) << (8 * k);
-                    }
-                }
-                dst[j] = x;
-            }
+    // Phase 1: stage rows seq0 .. seq0+rows-1 densely; zeros after them.
+    if (copy_mode == kCopyVec16) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(seqs + seq0 * (size_t)m);
+        uint4 *dst = reinterpret_cast<uint4 *>(sm);
+        const int nvec = nbytes >> 4;
+        int k = tid;
+        for (; k + 3 * kPackThreads < nvec; k += 4 * kPackThreads) {
+            const uint4 a = __ldg(src + k), b = __ldg(src + k + kPackThreads);
+            const uint4 c = __ldg(src + k + 2 * kPackThreads), d = __ldg(src + k + 3 * kPackThreads);
+            dst[k] = a;
+            dst[k + kPackThreads] = b;
+            dst[k + 2 * kPackThreads] = c;
+            dst[k + 3 * kPackThreads] = d;
         }
+        for (; k < nvec; k += kPackThreads)
+            dst[k] = __ldg(src + k);
+        for (int b = (nvec << 4) + tid; b < nbytes; b += kPackThreads)
+            sb[b] = __ldg(seqs + seq0 * (size_t)m + b);
+    } else if (copy_mode == kCopyVec4) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(seqs + seq0 * (size_t)m);
+        const int nw = nbytes >> 2;
+        int k = tid;
+        for (; k + 3 * kPackThreads < nw; k += 4 * kPackThreads) {
+            const uint32_t a = __ldg(src + k), b = __ldg(src + k + kPackThreads);
+            const uint32_t c = __ldg(src + k + 2 * kPackThreads), d = __ldg(src + k + 3 * kPackThreads);
+            sm[k] = a;
+            sm[k + kPackThreads] = b;
+            sm[k + 2 * kPackThreads] = c;
+            sm[k + 3 * kPackThreads] = d;
+        }
+        for (; k < nw; k += kPackThreads)
+            sm[k] = __ldg(src + k);
+        for (int b = (nw << 2) + tid; b < nbytes; b += kPackThreads)
+            sb[b] = __ldg(seqs + seq0 * (size_t)m + b);
     } else {
-        for (int r = warp; r < kPackSeqs; r += kPackThreads / 32) {
-            uint8_t *dst = (uint8_t *)(sm + row_word(r, W));
-            size_t s = seq0 + r;
-            const uint8_t *src = seqs + s * stride;
-            for (int j = ln; j < 4 * W; j += 32)
-                dst[j] = (s < n && j < m) ? __ldg(src + j) : (uint8_t)0;
+        const int warp = tid >> 5, ln = tid & 31;
+        for (int r = warp; r < rows; r += kPackThreads / 32) {
+            const uint8_t *src = seqs + (seq0 + r) * stride;
+            for (int j = ln; j < m; j += 32)
+                sb[r * m + j] = __ldg(src + j);
         }
     }
+    for (int b = nbytes + tid; b < total; b += kPackThreads)
+        sb[b] = 0;
     __syncthreads();
 
     // Phase 2.
-    for (int item = threadIdx.x; item < 8 * W; item += kPackThreads) {
+    const int J = (m + 3) >> 2;
+    for (int item = tid; item < 8 * J; item += kPackThreads) {
         const int l = item & 7, j = item >> 3;
+        const int rot = (rot_step * l) & 31;     // visit sequence (s + rot) % 32 at step s
         uint32_t yh[4], yl[4], yn[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             uint32_t h = 0, lo = 0, nn = 0;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int s = 8 * t + u;
-                const uint32_t w = sm[row_word(32 * l + s, W) + j];
-                // bit 2 -> bit u, bit 1 -> bit u, bit 7 (is N) -> bit u of each byte
+                const int s = (8 * t + u + rot) & 31;
+                const int o = (32 * l + s) * m + 4 * j;   // byte offset of the 4 bases
+                uint32_t w;
+                if (ALIGNED) {
+                    w = sm[o >> 2];
+                } else {
+                    w = __funnelshift_r(sm[o >> 2], sm[(o >> 2) + 1], 8 * (o & 3));
+                }
                 h |= ((w >> 2) & 0x01010101u) << u;
                 lo |= ((w >> 1) & 0x01010101u) << u;
                 if (WITH_N)
@@ -125,12 +155,61 @@ pack_kernel(const uint8_t *__restrict__ seqs, uint64_t stride, size_t n, int m,
             const int p = 4 * j + q;
             if (p < m) {
                 const size_t wi = (tile * (size_t)m + p) * 32 + lane;
-                reinterpret_cast<uint2 *>(packed)[wi] = make_uint2(H[q], L[q]);
+                // bit k of H holds sequence (k + rot) % 32: rotate left by rot
+                reinterpret_cast<uint2 *>(packed)[wi] =
+                    make_uint2(__funnelshift_l(H[q], H[q], rot), __funnelshift_l(L[q], L[q], rot));
                 if (WITH_N)
-                    nmask[wi] = N[q];
+                    nmask[wi] = __funnelshift_l(N[q], N[q], rot);
             }
         }
     }
+}
+
+// Per-lane rotation step c with c * (m/4) = 4 (mod 32) when such a c exists
+// (then the 8 lanes x 4 positions of a warp read 32 distinct banks); 0 when
+// m is not a multiple of 4 or m/4 shares a factor 8 with 32.
+int rotation_step(int m)
+{
+    if (m % 4)
+        return 0;
+    const int W = m / 4;
+    for (int c = 0; c < 32; ++c)
+        if ((c * W) % 32 == 4)
+            return c;
+    return 0;
+}
+
+template <bool WITH_N>
+cudaError_t launch_pack_t(const uint8_t *seqs, uint64_t stride, size_t n, int m,
+                          uint32_t *packed, uint32_t *nmask, cudaStream_t s)
+{
+    const size_t smem = (size_t)kPackSeqs * m + 16;
+    const size_t blocks = tiles_of(n) * (kTile / kPackSeqs);
+    int mode = kCopyRows;
+    if (stride == (uint64_t)m) {
+        if ((uintptr_t)seqs % 16 == 0)
+            mode = kCopyVec16;
+        else if ((uintptr_t)seqs % 4 == 0 && m % 4 == 0)
+            mode = kCopyVec4;
+    }
+    const int rot = rotation_step(m);
+    cudaError_t e;
+    if (m % 4 == 0) {
+        e = cudaFuncSetAttribute(pack_kernel<WITH_N, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        pack_kernel<WITH_N, true><<<(unsigned)blocks, kPackThreads, smem, s>>>(
+            seqs, stride, n, m, packed, nmask, mode, rot);
+    } else {
+        e = cudaFuncSetAttribute(pack_kernel<WITH_N, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        pack_kernel<WITH_N, false><<<(unsigned)blocks, kPackThreads, smem, s>>>(
+            seqs, stride, n, m, packed, nmask, mode, rot);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -138,23 +217,9 @@ pack_kernel(const uint8_t *__restrict__ seqs, uint64_t stride, size_t n, int m,
 cudaError_t launch_pack(const uint8_t *seqs, uint64_t stride, size_t n, int m,
                         uint32_t *packed, uint32_t *nmask, cudaStream_t s)
 {
-    const int W = (m + 3) / 4;
-    const size_t smem = (size_t)kPackSeqs * W * 4 + 8 * 4 * 4;
-    const size_t blocks = tiles_of(n) * (kTile / kPackSeqs);
-    const int word_rows = ((uintptr_t)seqs % 4 == 0) && (stride % 4 == 0);
-    cudaError_t e;
-    if (nmask) {
-        e = cudaFuncSetAttribute(pack_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        pack_kernel<true><<<(unsigned)blocks, kPackThreads, smem, s>>>(seqs, stride, n, m, packed, nmask, word_rows);
-    } else {
-        e = cudaFuncSetAttribute(pack_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        pack_kernel<false><<<(unsigned)blocks, kPackThreads, smem, s>>>(seqs, stride, n, m, packed, nullptr, word_rows);
-    }
-    return cudaGetLastError();
+    if (nmask)
+        return launch_pack_t<true>(seqs, stride, n, m, packed, nmask, s);
+    return launch_pack_t<false>(seqs, stride, n, m, packed, nmask, s);
 }
 
 }  // namespace shouji
