@@ -196,22 +196,38 @@ struct View {
     int m;
 };
 
+// Map columns that a chunk hands to the next one: window c needs columns
+// c..c+3, so consecutive chunks of U windows share 3 columns per diagonal.
+// Keeping them in registers saves 3 of every U+3 map evaluations; for large
+// E the 3(2E+1) extra live registers cost more than they save, and the
+// shared columns are recomputed instead.
+template <int E>
+struct Carry {
+    static constexpr bool kOn = E <= 8;
+    uint32_t M[kOn ? 2 * E + 1 : 1][3];
+};
+
 // One chunk of U windows starting at c0.
 //   BOUNDS: columns and read positions may fall outside [0, m) (edge chunks);
-//           an unbounded chunk needs c0 - E >= 0 and c0 + U + 2 + E < m.
+//           an unbounded chunk needs every column it evaluates and every read
+//           position those columns touch inside [0, m).
 //   MASKS:  N masks and/or per-pair thresholds are present.
+// With a carry, the chunk evaluates the U columns c0+3..c0+U+2 and takes
+// c0..c0+2 from the carry; without, it evaluates all U+3 columns c0..c0+U+2.
 template <int E, int U, bool BOUNDS, bool MASKS>
 __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[E + 1], int c0,
-                                      uint32_t &s0, uint32_t &s1, uint32_t &s2,
+                                      Carry<E> &carry, uint32_t &s0, uint32_t &s1, uint32_t &s2,
                                       uint32_t (&C)[8])
 {
-    constexpr int NC = U + 3;        // columns c0 .. c0+U+2
-    constexpr int NR = NC + 2 * E;   // read positions c0-E .. c0+U+2+E
+    constexpr bool CARRY = Carry<E>::kOn;
+    constexpr int K0 = CARRY ? 3 : 0;   // first evaluated column offset
+    constexpr int NC = U + 3 - K0;      // evaluated columns c0+K0 .. c0+U+2
+    constexpr int NR = NC + 2 * E;      // read positions c0+K0-E .. c0+U+2+E
     uint32_t th[NC], tl[NC], tx[MASKS ? NC : 1];
     uint32_t rh[NR], rl[NR], rx[MASKS ? NR : 1];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-        const int p = c0 + k;
+        const int p = c0 + K0 + k;
         const bool ok = !BOUNDS || p < v.m;
         const uint2 w = ok ? __ldg(v.rf + (size_t)p * 32) : make_uint2(0u, 0u);
         th[k] = w.x;
@@ -221,7 +237,7 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
     }
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
-        const int q = c0 - E + i;
+        const int q = c0 + K0 - E + i;
         const bool ok = !BOUNDS || (q >= 0 && q < v.m);
         const uint2 w = ok ? __ldg(v.rd + (size_t)q * 32) : make_uint2(0u, 0u);
         rh[i] = w.x;
@@ -230,35 +246,48 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
             rx[i] = (ok && v.rdn) ? __ldg(v.rdn + (size_t)q * 32) : 0u;
     }
 
-    // Mismatch bits of diagonal d at the chunk's column k.
+    // Mismatch bits of diagonal d at evaluated column k (column c0+K0+k).
     auto column = [&](int d, int k) -> uint32_t {
         const int i = k - d + E;
         uint32_t x = (th[k] ^ rh[i]) | (tl[k] ^ rl[i]);
         if constexpr (MASKS)
             x |= tx[k] | rx[i] | inactive[d < 0 ? -d : d];
         if constexpr (BOUNDS) {
-            const int p = c0 + k, q = c0 - E + i;
+            const int p = c0 + K0 + k, q = p - d;
             if (p >= v.m || q < 0 || q >= v.m)
                 x = ~0u;
         }
         return x;
     };
+    // All U+3 columns of diagonal d for this chunk; the last 3 become the
+    // next chunk's carry.
+    auto columns = [&](int d, uint32_t (&M)[U + 3]) {
+        if constexpr (CARRY) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                M[k] = carry.M[d + E][k];
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            M[K0 + k] = column(d, k);
+        if constexpr (CARRY) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                carry.M[d + E][k] = M[U + k];
+        }
+    };
 
     Pick pick[U];
     if constexpr (E == 0) {
-        uint32_t M[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k)
-            M[k] = column(0, k);
+        uint32_t M[U + 3];
+        columns(0, M);
 #pragma unroll
         for (int w = 0; w < U; ++w)
             pick[w] = make_pick(M[w], M[w + 1], M[w + 2], M[w + 3]);
     } else {
         {
-            uint32_t M[NC];
-#pragma unroll
-            for (int k = 0; k < NC; ++k)
-                M[k] = column(-1, k);
+            uint32_t M[U + 3];
+            columns(-1, M);
 #pragma unroll
             for (int w = 0; w < U; ++w)
                 pick[w] = make_pick(M[w], M[w + 1], M[w + 2], M[w + 3]);
@@ -270,19 +299,15 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
                 const int d = side ? j : -j;
                 if (d == -1)
                     continue;
-                uint32_t M[NC];
-#pragma unroll
-                for (int k = 0; k < NC; ++k)
-                    M[k] = column(d, k);
+                uint32_t M[U + 3];
+                columns(d, M);
 #pragma unroll
                 for (int w = 0; w < U; ++w)
                     offer(pick[w], M[w], M[w + 1], M[w + 2], M[w + 3]);
             }
         }
-        uint32_t M[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k)
-            M[k] = column(0, k);
+        uint32_t M[U + 3];
+        columns(0, M);
 #pragma unroll
         for (int w = 0; w < U; ++w)
             offer_main(pick[w], M[w], M[w + 1], M[w + 2], M[w + 3]);
@@ -316,6 +341,34 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
         const uint32_t x0 = fs ^ out[w + 3];
         const uint32_t t = fs & out[w + 3];
         counter_add3(C, x0, fc ^ t, fc & t);
+    }
+}
+
+// Columns 0..2 of every diagonal: the carry the first chunk starts from.
+template <int E, bool MASKS>
+__device__ __forceinline__ void carry_prologue(const View &v, const uint32_t (&inactive)[E + 1],
+                                               Carry<E> &carry)
+{
+    if constexpr (Carry<E>::kOn) {
+#pragma unroll
+        for (int d = -E; d <= E; ++d) {
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const int q = p - d;
+                uint32_t x = ~0u;
+                if (p < v.m && q >= 0 && q < v.m) {
+                    const uint2 t = __ldg(v.rf + (size_t)p * 32);
+                    const uint2 r = __ldg(v.rd + (size_t)q * 32);
+                    x = (t.x ^ r.x) | (t.y ^ r.y);
+                    if constexpr (MASKS) {
+                        if (v.rfn)
+                            x |= __ldg(v.rfn + (size_t)p * 32) | __ldg(v.rdn + (size_t)q * 32);
+                        x |= inactive[d < 0 ? -d : d];
+                    }
+                }
+                carry.M[d + E][p] = x;
+            }
+        }
     }
 }
 
@@ -364,15 +417,18 @@ filter_kernel(FilterArgs a)
     for (int i = 0; i < 8; ++i)
         C[i] = 0u;
 
+    Carry<E> carry;
+    carry_prologue<E, MASKS>(v, inactive, carry);
+    constexpr int K0 = Carry<E>::kOn ? 3 : 0;
     if constexpr (MASKS) {
         for (int c0 = 0; c0 < m; c0 += U)
-            chunk<E, U, true, true>(v, inactive, c0, s0, s1, s2, C);
+            chunk<E, U, true, true>(v, inactive, c0, carry, s0, s1, s2, C);
     } else {
         for (int c0 = 0; c0 < m; c0 += U) {
-            if ((c0 - E >= 0) && (c0 + U + 2 + E < m))
-                chunk<E, U, false, false>(v, inactive, c0, s0, s1, s2, C);
+            if ((c0 + K0 - E >= 0) && (c0 + U + 2 + E < m))
+                chunk<E, U, false, false>(v, inactive, c0, carry, s0, s1, s2, C);
             else
-                chunk<E, U, true, false>(v, inactive, c0, s0, s1, s2, C);
+                chunk<E, U, true, false>(v, inactive, c0, carry, s0, s1, s2, C);
         }
     }
 
