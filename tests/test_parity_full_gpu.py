@@ -1,0 +1,66 @@
+"""Parity at full workload sizes, in the launch sequence bench.py times.
+
+30M pairs at m=100 (sweep recipe, E = 0, 5, 10) and 10M pairs at m=150 / 250
+with 'N' bases: every pair is filtered on the GPU; a seeded sample of pairs is
+recomputed by the oracle one by one and must match bit for bit, and properties
+that hold for every pair are checked over the whole batch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1809_07858_gb300 as sj
+from paper_1809_07858_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+SAMPLE = 200_000
+
+
+def run_full(reads, refs, m, E, with_n):
+    dev = torch.device("cuda:0")
+    n = len(reads)
+    r = torch.from_numpy(reads).to(dev)
+    t = torch.from_numpy(refs).to(dev)
+    pr, nr = sj.shouji_pack(r, m, with_n=with_n)
+    pt, nt = sj.shouji_pack(t, m, with_n=with_n)
+    del r, t
+    acc, cnt, _ = sj.shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt)
+    idx, n_acc = sj.shouji_compact(acc, n)
+    torch.cuda.synchronize()
+    accept = sj.accept_to_bool(acc, n).cpu().numpy()
+    count = cnt[:n].cpu().numpy()
+    k = int(n_acc.item())
+    survivors = idx[:k].cpu().numpy()
+    return accept, count, survivors
+
+
+def check(reads, refs, m, E, with_n, seed):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n = len(reads)
+    accept, count, survivors = run_full(reads, refs, m, E, with_n)
+    # properties over every pair
+    assert (count <= m).all()
+    assert (accept == (count <= E)).all()
+    assert len(survivors) == int(accept.sum())
+    assert (np.diff(survivors.astype(np.int64)) > 0).all()
+    assert accept[survivors].all()
+    # the oracle on a seeded sample
+    pick = np.sort(np.random.default_rng(seed).choice(n, size=min(SAMPLE, n), replace=False))
+    acc_o, cnt_o = oracle.shouji_batch(reads[pick], refs[pick], E, threads=16)
+    assert (count[pick] == cnt_o).all()
+    assert (accept[pick] == acc_o).all()
+
+
+@pytest.mark.parametrize("E", [0, 5, 10])
+def test_sweep_30M(E):
+    reads, refs = synth.workload("sweep", 30_000_000, E=E)
+    check(reads, refs, 100, E, False, seed=E)
+
+
+@pytest.mark.parametrize("m,E", [(150, 15), (250, 15)])
+def test_long_10M_with_N(m, E):
+    reads, refs = synth.workload("long", 10_000_000, m=m, E=E)
+    check(reads, refs, m, E, True, seed=m)
