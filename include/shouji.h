@@ -176,6 +176,35 @@ shouji_status shouji_compact(const uint32_t *accept, size_t n_pairs,
                              void *stream);
 
 /*
+ * shouji_compact_noalloc -- shouji_compact without a caller-supplied
+ * workspace.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc, such as a program whose device memory
+ * is entirely owned by another allocator with a fixed budget, or a
+ * latency-bound loop that must not call cudaMalloc/cudaFree because they can
+ * synchronize the device.  It allocates nothing and calls no allocating
+ * routine.
+ *
+ * Its workspace is a fixed 16 KB __device__ array inside libshouji.so, held
+ * on every GPU that loads the library until the process exits.  The first
+ * call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  Every call on a device shares the one array:
+ * two calls whose work overlaps on the GPU (e.g. on two streams) race and
+ * may return wrong indices; serialize them.  The array keeps the last
+ * call's contents, and nothing in it needs to start at zero.
+ *
+ *   accept, n_pairs, out_idx, out_n, stream: as shouji_compact.
+ * Errors: SHOUJI_EINVAL for n_pairs > SHOUJI_NOALLOC_MAX_PAIRS (2^29) or
+ * NULL pointers (with n_pairs > 0); SHOUJI_ECUDA on a failed address lookup
+ * or launch.
+ */
+#define SHOUJI_NOALLOC_MAX_PAIRS ((size_t)1 << 29)
+
+shouji_status shouji_compact_noalloc(const uint32_t *accept, size_t n_pairs,
+                                     uint32_t *out_idx, uint32_t *out_n,
+                                     void *stream);
+
+/*
  * Host pipeline -- the whole filter for pairs held in HOST memory.
  *
  * The paper's accelerator receives pairs from the host and returns one

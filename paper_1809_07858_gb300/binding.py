@@ -17,13 +17,14 @@ LIB_PATH = os.path.join(HERE, "libshouji.so")
 SHOUJI_TILE = 1024
 SHOUJI_MAX_M = 255
 SHOUJI_MAX_E = 31
+SHOUJI_NOALLOC_MAX_PAIRS = 1 << 29
 
 __all__ = [
     "ShoujiError", "SHOUJI_TILE", "SHOUJI_MAX_M", "SHOUJI_MAX_E", "LIB_PATH",
     "load_library", "shouji_status_string", "shouji_last_cuda_error",
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
-    "accept_to_bool", "Pipeline",
+    "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
 ]
 
 _lib = None
@@ -63,6 +64,8 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_compact_workspace_size.restype = sz
     lib.shouji_compact.argtypes = [vp, sz, vp, vp, vp, sz, vp]
     lib.shouji_compact.restype = ctypes.c_int
+    lib.shouji_compact_noalloc.argtypes = [vp, sz, vp, vp, vp]
+    lib.shouji_compact_noalloc.restype = ctypes.c_int
     lib.shouji_pipeline_create.argtypes = [u32, sz, sz, ctypes.c_int, ctypes.POINTER(vp)]
     lib.shouji_pipeline_create.restype = ctypes.c_int
     lib.shouji_pipeline_run.argtypes = [vp, vp, vp, u64, sz, ctypes.c_int, vp, vp, vp,
@@ -187,6 +190,21 @@ def shouji_compact(accept, n_pairs: int, *, out_idx=None, out_n=None, workspace=
     _check(lib.shouji_compact(_ptr(accept), n_pairs, _ptr(out_idx), _ptr(out_n),
                               _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _stream(stream)), "shouji_compact")
+    return out_idx, out_n
+
+
+def shouji_compact_noalloc(accept, n_pairs: int, *, out_idx=None, out_n=None, stream=None):
+    """Like ``shouji_compact`` but with the library's own fixed device
+    workspace (no allocation by the library).  Returns ``(idx, n_dev)``."""
+    torch = _torch()
+    lib = load_library()
+    dev = accept.device
+    if out_idx is None:
+        out_idx = torch.empty(max(1, n_pairs), dtype=torch.int32, device=dev)
+    if out_n is None:
+        out_n = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(lib.shouji_compact_noalloc(_ptr(accept), n_pairs, _ptr(out_idx), _ptr(out_n),
+                                      _stream(stream)), "shouji_compact_noalloc")
     return out_idx, out_n
 
 
