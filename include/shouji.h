@@ -253,6 +253,82 @@ shouji_status shouji_pipeline_run(shouji_pipeline *pipeline,
 
 void shouji_pipeline_destroy(shouji_pipeline *pipeline);
 
+/*
+ * Batched filter -- pairs of mixed lengths and thresholds in one launch.
+ *
+ * The work per pair grows with m (2E + 2) (Eq. 2 of the paper), and the
+ * 32 pairs that share a bit-sliced group cost as much as their longest,
+ * most tolerant member.  A batch object therefore buckets each batch on the
+ * device by (m, E), packs every bucket, runs one persistent filter kernel per
+ * threshold over all of its buckets and gathers the results back to input
+ * order.  The whole sequence is captured once into a CUDA graph; every run
+ * is one graph launch.  The global mode of the paper applies: a pair's read
+ * and reference have the same length (Supp. Sec. 8).
+ *
+ * shouji_batch_create allocates every device buffer on the current device.
+ *   max_pairs    largest batch (< 2^31).
+ *   max_m        longest sequence, <= SHOUJI_MAX_M.
+ *   e_min, e_max thresholds the batches may use (0 <= e_min <= e_max <= 31);
+ *                one filter kernel per threshold in the range is in the graph.
+ *   with_n       nonzero: 'N' matches nothing (N masks are built).
+ *   tune_cache   path of a tuning cache written by shouji_batch_tune, or NULL
+ *                (defaults: 128 threads, 4 CTAs per SM, strided schedule).
+ * Errors: SHOUJI_EINVAL, SHOUJI_ENOMEM (nothing leaked), SHOUJI_ECUDA.
+ *
+ * shouji_batch_run filters one batch, asynchronously on `stream`.  Device
+ * pointers:
+ *   reads, refs   n_pairs rows, row i at + i * stride, lens[i] bases each;
+ *                 each buffer must be readable for n_pairs * stride bytes
+ *                 (whole 16-byte chunks are read when stride is a multiple of
+ *                 16 no smaller than max_m rounded up to 16).
+ *   lens          uint16[n_pairs], each in [1, max_m].
+ *   E_per_pair    uint8[n_pairs], each in [e_min, e_max].
+ *   out_accept    uint32[ceil(n_pairs / 32)] (layout of shouji_filter).
+ *   out_count     uint8[n_pairs] or NULL.
+ * A pair whose length or threshold is out of range is rejected (accept 0,
+ * count 255) and counted by shouji_batch_invalid.  Before it writes a new
+ * argument block, a run waits until the previous run of the same object has
+ * started on the GPU; one object runs one batch at a time, and concurrent
+ * batches need one object each.
+ * Errors: SHOUJI_EINVAL (nothing launched), SHOUJI_ECUDA.
+ *
+ * shouji_batch_invalid waits for the last run and returns its number of
+ * rejected out-of-range pairs.
+ *
+ * shouji_batch_tune is the autotuner.  It runs the bucketing and packing of
+ * the given batch, then times every launch shape of each threshold's filter
+ * kernel (CTA of 64 or 128 threads, 1-8 CTAs per SM; groups grid-strided,
+ * in a contiguous range per CTA, or taken from a shared counter) and keeps
+ * the fastest.  It appends them to tune_cache
+ * (when not NULL) as "<gpu> <E> <threads> <ctas/SM> <schedule> <ms>" lines,
+ * which shouji_batch_create reads back.  It does not write out_accept /
+ * out_count: call shouji_batch_run afterwards.  It synchronizes `stream`.
+ *
+ * shouji_batch_destroy waits for the last run and frees everything.
+ */
+typedef struct shouji_batch shouji_batch;
+
+shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min,
+                                  int e_max, int with_n, const char *tune_cache,
+                                  shouji_batch **out);
+
+shouji_status shouji_batch_run(shouji_batch *batch, const uint8_t *reads,
+                               const uint8_t *refs, uint64_t stride,
+                               const uint16_t *lens, const uint8_t *E_per_pair,
+                               size_t n_pairs, uint32_t *out_accept,
+                               uint8_t *out_count, void *stream);
+
+shouji_status shouji_batch_invalid(shouji_batch *batch, uint64_t *n_invalid);
+
+shouji_status shouji_batch_tune(shouji_batch *batch, const uint8_t *reads,
+                                const uint8_t *refs, uint64_t stride,
+                                const uint16_t *lens, const uint8_t *E_per_pair,
+                                size_t n_pairs, uint32_t *out_accept,
+                                uint8_t *out_count, const char *tune_cache,
+                                void *stream);
+
+void shouji_batch_destroy(shouji_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

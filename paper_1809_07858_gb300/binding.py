@@ -25,6 +25,7 @@ __all__ = [
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
+    "Batch",
 ]
 
 _lib = None
@@ -66,6 +67,17 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_compact.restype = ctypes.c_int
     lib.shouji_compact_noalloc.argtypes = [vp, sz, vp, vp, vp]
     lib.shouji_compact_noalloc.restype = ctypes.c_int
+    lib.shouji_batch_create.argtypes = [sz, u32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_char_p, ctypes.POINTER(vp)]
+    lib.shouji_batch_create.restype = ctypes.c_int
+    lib.shouji_batch_run.argtypes = [vp, vp, vp, u64, vp, vp, sz, vp, vp, vp]
+    lib.shouji_batch_run.restype = ctypes.c_int
+    lib.shouji_batch_invalid.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.shouji_batch_invalid.restype = ctypes.c_int
+    lib.shouji_batch_tune.argtypes = [vp, vp, vp, u64, vp, vp, sz, vp, vp, ctypes.c_char_p, vp]
+    lib.shouji_batch_tune.restype = ctypes.c_int
+    lib.shouji_batch_destroy.argtypes = [vp]
+    lib.shouji_batch_destroy.restype = None
     lib.shouji_pipeline_create.argtypes = [u32, sz, sz, ctypes.c_int, ctypes.POINTER(vp)]
     lib.shouji_pipeline_create.restype = ctypes.c_int
     lib.shouji_pipeline_run.argtypes = [vp, vp, vp, u64, sz, ctypes.c_int, vp, vp, vp,
@@ -274,6 +286,74 @@ class Pipeline:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load_library().shouji_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """``shouji_batch_*``: pairs of mixed lengths and thresholds, bucketed,
+    packed and filtered on the device in one CUDA-graph launch per batch.
+
+    Tensors are CUDA tensors: ``reads``/``refs`` (n, stride) uint8, ``lens``
+    int16/uint16-compatible int16 tensor or numpy-converted, ``E_per_pair``
+    uint8.
+    """
+
+    def __init__(self, max_pairs: int, max_m: int, e_min: int, e_max: int,
+                 with_n: bool = False, tune_cache: str | None = None):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.shouji_batch_create(max_pairs, max_m, e_min, e_max, int(with_n),
+                                       tune_cache.encode() if tune_cache else None,
+                                       ctypes.byref(h)), "shouji_batch_create")
+        self._h = h
+        self.max_pairs = max_pairs
+
+    def _args(self, reads, refs, lens, E_per_pair, n_pairs, stride, out_accept, out_count):
+        torch = _torch()
+        dev = reads.device
+        n = reads.shape[0] if n_pairs is None else n_pairs
+        stride = reads.shape[1] if stride is None else stride
+        if out_accept is None:
+            out_accept = torch.empty(max(1, (n + 31) // 32), dtype=torch.int32, device=dev)
+        return n, stride, out_accept, out_count
+
+    def run(self, reads, refs, lens, E_per_pair, *, n_pairs=None, stride=None,
+            out_accept=None, out_count=None, count: bool = True, stream=None):
+        """Returns ``(accept_words, count)``."""
+        torch = _torch()
+        n, stride, out_accept, out_count = self._args(reads, refs, lens, E_per_pair, n_pairs,
+                                                      stride, out_accept, out_count)
+        if out_count is None and count:
+            out_count = torch.empty(max(1, n), dtype=torch.uint8, device=reads.device)
+        _check(load_library().shouji_batch_run(
+            self._h, _ptr(reads), _ptr(refs), stride, _ptr(lens), _ptr(E_per_pair), n,
+            _ptr(out_accept), _ptr(out_count), _stream(stream)), "shouji_batch_run")
+        return out_accept, out_count
+
+    def tune(self, reads, refs, lens, E_per_pair, *, n_pairs=None, stride=None,
+             cache: str | None = None, stream=None):
+        n, stride, out_accept, _ = self._args(reads, refs, lens, E_per_pair, n_pairs, stride,
+                                              None, None)
+        _check(load_library().shouji_batch_tune(
+            self._h, _ptr(reads), _ptr(refs), stride, _ptr(lens), _ptr(E_per_pair), n,
+            _ptr(out_accept), None, cache.encode() if cache else None, _stream(stream)),
+            "shouji_batch_tune")
+
+    def invalid(self) -> int:
+        v = ctypes.c_uint64(0)
+        _check(load_library().shouji_batch_invalid(self._h, ctypes.byref(v)),
+               "shouji_batch_invalid")
+        return v.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().shouji_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

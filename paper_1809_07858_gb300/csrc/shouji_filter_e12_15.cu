@@ -7,4 +7,8 @@ template cudaError_t launch_filter_E<12>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<13>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<14>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<15>(const FilterArgs &, cudaStream_t);
+template cudaError_t batch::launch_filter_E<12>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<13>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<14>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<15>(const batch::FilterParams &, int, int, cudaStream_t);
 }  // namespace shouji

@@ -7,4 +7,8 @@ template cudaError_t launch_filter_E<16>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<17>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<18>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<19>(const FilterArgs &, cudaStream_t);
+template cudaError_t batch::launch_filter_E<16>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<17>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<18>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<19>(const batch::FilterParams &, int, int, cudaStream_t);
 }  // namespace shouji

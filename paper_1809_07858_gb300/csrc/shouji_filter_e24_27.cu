@@ -7,4 +7,8 @@ template cudaError_t launch_filter_E<24>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<25>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<26>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<27>(const FilterArgs &, cudaStream_t);
+template cudaError_t batch::launch_filter_E<24>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<25>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<26>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<27>(const batch::FilterParams &, int, int, cudaStream_t);
 }  // namespace shouji

@@ -7,4 +7,8 @@ template cudaError_t launch_filter_E<28>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<29>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<30>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<31>(const FilterArgs &, cudaStream_t);
+template cudaError_t batch::launch_filter_E<28>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<29>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<30>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<31>(const batch::FilterParams &, int, int, cudaStream_t);
 }  // namespace shouji

@@ -7,4 +7,8 @@ template cudaError_t launch_filter_E<8>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<9>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<10>(const FilterArgs &, cudaStream_t);
 template cudaError_t launch_filter_E<11>(const FilterArgs &, cudaStream_t);
+template cudaError_t batch::launch_filter_E<8>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<9>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<10>(const batch::FilterParams &, int, int, cudaStream_t);
+template cudaError_t batch::launch_filter_E<11>(const batch::FilterParams &, int, int, cudaStream_t);
 }  // namespace shouji

@@ -20,34 +20,15 @@
 // output word is rotated back.  Stores are 32-byte (N mask) or 64-byte
 // (planes) contiguous segments.
 #include "shouji_internal.cuh"
+#include "shouji_pack.cuh"
 
 namespace shouji {
 namespace {
 
+using namespace packdev;
+
 constexpr int kPackThreads = 256;
 constexpr int kPackSeqs = 256;  // 8 lanes
-
-// 4x4 byte transpose: out[q] byte u = in[u] byte q.
-__device__ __forceinline__ void transpose4x4(uint32_t y0, uint32_t y1, uint32_t y2,
-                                             uint32_t y3, uint32_t out[4])
-{
-    uint32_t a = __byte_perm(y0, y1, 0x5140);
-    uint32_t b = __byte_perm(y0, y1, 0x7362);
-    uint32_t c = __byte_perm(y2, y3, 0x5140);
-    uint32_t d = __byte_perm(y2, y3, 0x7362);
-    out[0] = __byte_perm(a, c, 0x5410);
-    out[1] = __byte_perm(a, c, 0x7632);
-    out[2] = __byte_perm(b, d, 0x5410);
-    out[3] = __byte_perm(b, d, 0x7632);
-}
-
-// Bit 7 of each byte of the result = that byte of w equals 'N' (0x4E).
-__device__ __forceinline__ uint32_t n_bytes(uint32_t w)
-{
-    uint32_t x = w ^ 0x4E4E4E4Eu;
-    uint32_t t = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
-    return ~t & 0x80808080u;
-}
 
 enum CopyMode { kCopyVec16 = 0, kCopyVec4 = 1, kCopyRows = 2 };
 
@@ -116,67 +97,7 @@ pack_kernel(const uint8_t *__restrict__ seqs, uint64_t stride, size_t n, int m,
         sb[b] = 0;
     __syncthreads();
 
-    // Phase 2.
-    const int J = (m + 3) >> 2;
-    for (int item = tid; item < 8 * J; item += kPackThreads) {
-        const int l = item & 7, j = item >> 3;
-        const int rot = (rot_step * l) & 31;     // visit sequence (s + rot) % 32 at step s
-        uint32_t yh[4], yl[4], yn[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            uint32_t h = 0, lo = 0, nn = 0;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int s = (8 * t + u + rot) & 31;
-                const int o = (32 * l + s) * m + 4 * j;   // byte offset of the 4 bases
-                uint32_t w;
-                if (ALIGNED) {
-                    w = sm[o >> 2];
-                } else {
-                    w = __funnelshift_r(sm[o >> 2], sm[(o >> 2) + 1], 8 * (o & 3));
-                }
-                h |= ((w >> 2) & 0x01010101u) << u;
-                lo |= ((w >> 1) & 0x01010101u) << u;
-                if (WITH_N)
-                    nn |= (n_bytes(w) >> 7) << u;
-            }
-            yh[t] = h;
-            yl[t] = lo;
-            yn[t] = nn;
-        }
-        uint32_t H[4], L[4], N[4];
-        transpose4x4(yh[0], yh[1], yh[2], yh[3], H);
-        transpose4x4(yl[0], yl[1], yl[2], yl[3], L);
-        if (WITH_N)
-            transpose4x4(yn[0], yn[1], yn[2], yn[3], N);
-        const int lane = lane0 + l;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int p = 4 * j + q;
-            if (p < m) {
-                const size_t wi = (tile * (size_t)m + p) * 32 + lane;
-                // bit k of H holds sequence (k + rot) % 32: rotate left by rot
-                reinterpret_cast<uint2 *>(packed)[wi] =
-                    make_uint2(__funnelshift_l(H[q], H[q], rot), __funnelshift_l(L[q], L[q], rot));
-                if (WITH_N)
-                    nmask[wi] = __funnelshift_l(N[q], N[q], rot);
-            }
-        }
-    }
-}
-
-// Per-lane rotation step c with c * (m/4) = 4 (mod 32) when such a c exists
-// (then the 8 lanes x 4 positions of a warp read 32 distinct banks); 0 when
-// m is not a multiple of 4 or m/4 shares a factor 8 with 32.
-int rotation_step(int m)
-{
-    if (m % 4)
-        return 0;
-    const int W = m / 4;
-    for (int c = 0; c < 32; ++c)
-        if ((c * W) % 32 == 4)
-            return c;
-    return 0;
+    pack_transpose<WITH_N, ALIGNED>(sm, m, m, tile, lane0, packed, nmask, rot_step, kPackThreads);
 }
 
 template <bool WITH_N>

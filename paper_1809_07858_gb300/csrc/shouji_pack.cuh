@@ -1,0 +1,107 @@
+// Device helpers of shouji_pack, shared with the batched path.
+#pragma once
+
+#include "shouji_internal.cuh"
+
+namespace shouji {
+namespace packdev {
+
+// 4x4 byte transpose: out[q] byte u = in[u] byte q.
+__device__ __forceinline__ void transpose4x4(uint32_t y0, uint32_t y1, uint32_t y2,
+                                             uint32_t y3, uint32_t out[4])
+{
+    uint32_t a = __byte_perm(y0, y1, 0x5140);
+    uint32_t b = __byte_perm(y0, y1, 0x7362);
+    uint32_t c = __byte_perm(y2, y3, 0x5140);
+    uint32_t d = __byte_perm(y2, y3, 0x7362);
+    out[0] = __byte_perm(a, c, 0x5410);
+    out[1] = __byte_perm(a, c, 0x7632);
+    out[2] = __byte_perm(b, d, 0x5410);
+    out[3] = __byte_perm(b, d, 0x7632);
+}
+
+// Bit 7 of each byte of the result = that byte of w equals 'N' (0x4E).
+__device__ __forceinline__ uint32_t n_bytes(uint32_t w)
+{
+    uint32_t x = w ^ 0x4E4E4E4Eu;
+    uint32_t t = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
+    return ~t & 0x80808080u;
+}
+
+// Phase 2 of the pack: the staged rows (row r = sequence r of the block, at
+// byte r * rs of sm, m bases each) -> the bit-sliced words of lanes
+// lane0 .. lane0+LANES-1 of a tile.  A thread owns (lane, 4 consecutive
+// positions); a warp covers LANES lanes x 32/LANES position quads.
+// ALIGNED: rs % 4 == 0, so every 4-position word of a row is word-aligned.
+template <bool WITH_N, bool ALIGNED, int LANES = 8>
+__device__ __forceinline__ void pack_transpose(const uint32_t *__restrict__ sm, int m, int rs,
+                                               size_t tile, int lane0,
+                                               uint32_t *__restrict__ packed,
+                                               uint32_t *__restrict__ nmask, int rot_step,
+                                               int nthreads)
+{
+    const int J = (m + 3) >> 2;
+    for (int item = threadIdx.x; item < LANES * J; item += nthreads) {
+        const int l = item % LANES, j = item / LANES;
+        const int rot = (rot_step * l) & 31;     // visit sequence (s + rot) % 32 at step s
+        uint32_t yh[4], yl[4], yn[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            uint32_t h = 0, lo = 0, nn = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int s = (8 * t + u + rot) & 31;
+                const int o = (32 * l + s) * rs + 4 * j;   // byte offset of the 4 bases
+                uint32_t w;
+                if (ALIGNED) {
+                    w = sm[o >> 2];
+                } else {
+                    w = __funnelshift_r(sm[o >> 2], sm[(o >> 2) + 1], 8 * (o & 3));
+                }
+                h |= ((w >> 2) & 0x01010101u) << u;
+                lo |= ((w >> 1) & 0x01010101u) << u;
+                if (WITH_N)
+                    nn |= (n_bytes(w) >> 7) << u;
+            }
+            yh[t] = h;
+            yl[t] = lo;
+            yn[t] = nn;
+        }
+        uint32_t H[4], L[4], N[4];
+        transpose4x4(yh[0], yh[1], yh[2], yh[3], H);
+        transpose4x4(yl[0], yl[1], yl[2], yl[3], L);
+        if (WITH_N)
+            transpose4x4(yn[0], yn[1], yn[2], yn[3], N);
+        const int lane = lane0 + l;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int p = 4 * j + q;
+            if (p < m) {
+                const size_t wi = (tile * (size_t)m + p) * 32 + lane;
+                // bit k of H holds sequence (k + rot) % 32: rotate left by rot
+                reinterpret_cast<uint2 *>(packed)[wi] =
+                    make_uint2(__funnelshift_l(H[q], H[q], rot), __funnelshift_l(L[q], L[q], rot));
+                if (WITH_N)
+                    nmask[wi] = __funnelshift_l(N[q], N[q], rot);
+            }
+        }
+    }
+}
+
+// Per-lane rotation step c with c * (rs/4) = 32/lanes (mod 32) when such a c
+// exists (then the lanes x 32/lanes position quads of a warp read 32
+// distinct banks); 0 when the row stride rs is not a multiple of 4 or no
+// such c exists.
+__host__ __device__ inline int rotation_step(int rs, int lanes = 8)
+{
+    if (rs % 4)
+        return 0;
+    const int W = rs / 4, target = 32 / lanes;
+    for (int c = 0; c < 32; ++c)
+        if ((c * W) % 32 == target)
+            return c;
+    return 0;
+}
+
+}  // namespace packdev
+}  // namespace shouji

@@ -1,0 +1,137 @@
+"""The batched path (mixed lengths and thresholds in one CUDA-graph launch)
+against the oracle, pair by pair: accept bits and counts bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1809_07858_gb300 as sj
+from paper_1809_07858_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def oracle_mixed(reads, refs, lens, Es):
+    """Per pair: the oracle on the first lens[i] bases at threshold Es[i]."""
+    n = len(lens)
+    acc = np.zeros(n, bool)
+    cnt = np.zeros(n, np.uint8)
+    for L in np.unique(lens):
+        idx = np.flatnonzero(lens == L)
+        a, c = oracle.shouji_batch(reads[idx, :L], refs[idx, :L], 0,
+                                   E_per_pair=Es[idx].astype(np.uint8), threads=8)
+        acc[idx], cnt[idx] = a, c
+    return acc, cnt
+
+
+def accept_bits(words, n):
+    w = words.view(np.uint32)
+    return ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1)[:n].astype(bool)
+
+
+def run_batch(b, reads, refs, lens, Es, stride=None):
+    d = dev()
+    acc, cnt = b.run(torch.from_numpy(np.ascontiguousarray(reads)).to(d),
+                     torch.from_numpy(np.ascontiguousarray(refs)).to(d),
+                     torch.from_numpy(lens.astype(np.int16)).to(d),
+                     torch.from_numpy(Es.astype(np.uint8)).to(d), stride=stride)
+    torch.cuda.synchronize()
+    n = len(lens)
+    return accept_bits(acc.cpu().numpy(), n), cnt[:n].cpu().numpy()
+
+
+def mixed_batch(n, seed, n_rate=0.0, choices=(100, 150, 250), weights=(0.4, 0.4, 0.2),
+                e_range=(2, 12), stride=256):
+    lens, Es = synth.mixed_shape(n, seed=seed, choices=choices, weights=weights, e_range=e_range)
+    reads, refs = synth.pairs(n, max(choices), seed=seed, near=(0, 6), far=(7, 40),
+                              far_fraction=0.5, n_rate=n_rate, lengths=lens, stride=stride)
+    return reads, refs, lens, Es
+
+
+def test_mixed_lengths_and_thresholds_bit_exact():
+    reads, refs, lens, Es = mixed_batch(20_000, seed=1)
+    b = sj.Batch(50_000, 255, 2, 12)
+    acc, cnt = run_batch(b, reads, refs, lens, Es)
+    acc_o, cnt_o = oracle_mixed(reads, refs, lens, Es)
+    assert (cnt == cnt_o).all(), np.flatnonzero(cnt != cnt_o)[:10]
+    assert (acc == acc_o).all()
+    assert b.invalid() == 0
+    # the same object again, another batch of another size (graph reuse)
+    reads, refs, lens, Es = mixed_batch(7_777, seed=2)
+    acc, cnt = run_batch(b, reads, refs, lens, Es)
+    acc_o, cnt_o = oracle_mixed(reads, refs, lens, Es)
+    assert (cnt == cnt_o).all() and (acc == acc_o).all()
+    b.close()
+
+
+def test_every_length_and_threshold_with_N():
+    rng = np.random.default_rng(3)
+    n = 12_000
+    lens = rng.integers(1, 256, size=n).astype(np.uint16)
+    Es = rng.integers(0, 32, size=n).astype(np.uint8)
+    reads, refs = synth.pairs(n, 255, seed=3, near=(0, 8), far=(9, 60), far_fraction=0.5,
+                              n_rate=0.01, lengths=lens, stride=255)
+    b = sj.Batch(n, 255, 0, 31, with_n=True)
+    acc, cnt = run_batch(b, reads, refs, lens, Es)
+    acc_o, cnt_o = oracle_mixed(reads, refs, lens, Es)
+    assert (cnt == cnt_o).all(), np.flatnonzero(cnt != cnt_o)[:10]
+    assert (acc == acc_o).all()
+    b.close()
+
+
+def test_out_of_range_pairs_are_rejected_and_counted():
+    n = 3000
+    lens, Es = synth.mixed_shape(n, seed=4)
+    lens[::97] = 0          # length 0: out of range
+    lens[5::101] = 250      # in range
+    Es[7::89] = 13          # threshold above e_max
+    reads, refs = synth.pairs(n, 250, seed=4, near=(0, 6), far=(7, 40), far_fraction=0.5,
+                              lengths=lens, stride=256)
+    bad = (lens == 0) | (Es > 12)
+    b = sj.Batch(n, 250, 2, 12)
+    acc, cnt = run_batch(b, reads, refs, lens, Es)
+    assert b.invalid() == int(bad.sum())
+    assert (~acc[bad]).all() and (cnt[bad] == 255).all()
+    ok = ~bad
+    acc_o, cnt_o = oracle_mixed(reads[ok], refs[ok], lens[ok], Es[ok])
+    assert (cnt[ok] == cnt_o).all() and (acc[ok] == acc_o).all()
+    b.close()
+
+
+def test_tuned_shapes_give_identical_results(tmp_path):
+    reads, refs, lens, Es = mixed_batch(40_000, seed=5)
+    d = dev()
+    args = (torch.from_numpy(reads).to(d), torch.from_numpy(refs).to(d),
+            torch.from_numpy(lens.astype(np.int16)).to(d), torch.from_numpy(Es).to(d))
+    cache = str(tmp_path / "tune.txt")
+    b = sj.Batch(40_000, 255, 2, 12)
+    acc0, cnt0 = b.run(*args)
+    torch.cuda.synchronize()
+    acc0, cnt0 = acc0.cpu().clone(), cnt0.cpu().clone()
+    b.tune(*args, cache=cache)
+    acc1, cnt1 = b.run(*args)
+    torch.cuda.synchronize()
+    assert torch.equal(acc0, acc1.cpu()) and torch.equal(cnt0, cnt1.cpu())
+    lines = open(cache).read().split("\n")
+    assert sum(1 for l in lines if l.strip()) == 11     # E = 2..12 present in the batch
+    b2 = sj.Batch(40_000, 255, 2, 12, tune_cache=cache)   # reads the cache back
+    acc2, cnt2 = b2.run(*args)
+    torch.cuda.synchronize()
+    assert torch.equal(acc0, acc2.cpu()) and torch.equal(cnt0, cnt2.cpu())
+    b.close()
+    b2.close()
+
+
+def test_unaligned_stride_byte_path():
+    reads, refs, lens, Es = mixed_batch(5000, seed=6, stride=251)
+    b = sj.Batch(5000, 250, 2, 12)
+    acc, cnt = run_batch(b, reads, refs, lens, Es)
+    acc_o, cnt_o = oracle_mixed(reads, refs, lens, Es)
+    assert (cnt == cnt_o).all() and (acc == acc_o).all()
+    b.close()
