@@ -187,6 +187,129 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_batched(args, dev, peak_ops):
+    """The batched form: config-4-shaped batch of mixed lengths (40% 100, 40%
+    150, 20% 250) and per-pair E uniform in 2..12, unsorted, one CUDA-graph
+    launch per batch (bucketing, packing, per-threshold filters, gather)."""
+    import numpy as np
+    import torch
+
+    import paper_1809_07858_gb300 as sj
+    from paper_1809_07858_gb300 import synth
+    n = args.batched_n
+    lens, Es = synth.mixed_shape(n, seed=4242)
+    reads, refs = synth.pairs(n, 250, seed=4242, near=(0, 6), far=(7, 40), far_fraction=0.5,
+                              lengths=lens, stride=256)
+    ops = float(np.sum(lens.astype(np.float64) * (32.0 * Es.astype(np.float64) + 22.0) / 32.0))
+    d_reads = torch.from_numpy(reads).to(dev)
+    d_refs = torch.from_numpy(refs).to(dev)
+    del reads, refs
+    d_lens = torch.from_numpy(lens.astype(np.int16)).to(dev)
+    d_E = torch.from_numpy(Es).to(dev)
+    acc = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.uint8, device=dev)
+    b = sj.Batch(n, 250, 2, 12)
+    b.tune(d_reads, d_refs, d_lens, d_E)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        b.run(d_reads, d_refs, d_lens, d_E, out_accept=acc, out_count=cnt)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.batched_steps):
+        b.run(d_reads, d_refs, d_lens, d_E, out_accept=acc, out_count=cnt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.batched_steps
+    invalid = b.invalid()
+    b.close()
+    del d_reads, d_refs
+    torch.cuda.empty_cache()
+    achieved = ops / (ms * 1e-3)
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.batched_steps,
+            "workload": "%d pairs, lengths 40%% 100 / 40%% 150 / 20%% 250, E uniform 2..12, "
+                        "unsorted, stride 256, one CUDA-graph launch per batch (tuned)" % n,
+            "invalid": invalid,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
+                         "unit": "lane-ops/s", "frac": achieved / peak_ops,
+                         "scope": "whole batch step (bucketing, packing, filters, gather)"}}
+
+
+def run_served(args, dev):
+    """The served form: requests of log-uniform size in [1e3, 1e6] pairs with
+    the batched mix, arriving as a Poisson process at --serve-rate per second,
+    filtered by the server (continuous batching over memory-budgeted slots).
+    Latency = submit to results in host memory."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_1809_07858_gb300 as sj
+    from paper_1809_07858_gb300 import synth
+    pool = 1_200_000
+    lens, Es = synth.mixed_shape(pool, seed=777)
+    h_reads = torch.empty((pool, 256), dtype=torch.uint8, pin_memory=True)
+    h_refs = torch.empty((pool, 256), dtype=torch.uint8, pin_memory=True)
+    synth.pairs(pool, 250, seed=777, near=(0, 6), far=(7, 40), far_fraction=0.5, lengths=lens,
+                stride=256, out=(h_reads, h_refs))
+    h_lens = torch.from_numpy(lens.astype(np.int16)).pin_memory()
+    h_E = torch.from_numpy(Es).pin_memory()
+    rng = np.random.default_rng(99)
+    n_req = max(1, int(args.serve_rate * args.serve_seconds))
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=n_req)).astype(np.int64)
+    gaps = rng.exponential(1.0 / args.serve_rate, size=n_req)
+    offs = rng.integers(0, pool - sizes + 1)
+    ring = 64
+    outs = [(torch.empty(31_251, dtype=torch.int32, pin_memory=True),
+             torch.empty(1_000_000, dtype=torch.uint8, pin_memory=True)) for _ in range(ring)]
+    budget = int(args.serve_budget_gb * (1 << 30))
+    srv = sj.Server(1_000_000, 250, 2, 12, max_stride=256, memory_budget=budget,
+                    max_slots=args.serve_slots)
+    slots, per_slot = srv.info()
+    ids = [None] * n_req
+    ready = [threading.Event() for _ in range(n_req)]
+    lat = [0.0] * n_req
+    free = threading.Semaphore(ring)
+
+    def submitter():
+        t_next = time.perf_counter()
+        for i in range(n_req):
+            t_next += gaps[i]
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            free.acquire()
+            a, c = outs[i % ring]
+            o, k = int(offs[i]), int(sizes[i])
+            ids[i] = srv.submit(h_reads[o:o + k], h_refs[o:o + k], h_lens[o:o + k], h_E[o:o + k],
+                                a, c, n_pairs=k, stride=256)
+            ready[i].set()
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    for i in range(n_req):
+        ready[i].wait()
+        lat[i] = srv.wait(ids[i], timeout=120)
+        free.release()
+    t_end = time.perf_counter()
+    th.join()
+    srv.close()
+    wall = t_end - t0
+    total = int(sizes.sum())
+    lat_ms = np.array(lat) * 1e3
+    return {"value": total / wall, "unit": UNIT, "requests": n_req, "duration_s": wall,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "mean_request_pairs": float(sizes.mean()),
+            "offered_pairs_per_s": float(sizes.mean() * args.serve_rate),
+            "arrival": "Poisson, %g requests/s; sizes log-uniform in [1e3, 1e6] pairs; "
+                       "lengths 40%% 100 / 40%% 150 / 20%% 250, E uniform 2..12" % args.serve_rate,
+            "slots": slots, "bytes_per_slot": per_slot,
+            "memory_budget_gb": args.serve_budget_gb}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -308,6 +431,14 @@ def run_ours(args, world, rank, local):
     e2e_value = world * n * args.e2e_steps / e2e_s
     h2d = 2 * n * M
     d2h = h_acc.numel() * 4 + n + 4 * n_accepted
+    batched = served = None
+    if world == 1:
+        del d_reads, d_refs, packed_r, packed_t, idx
+        torch.cuda.empty_cache()
+        if args.batched_steps > 0:
+            batched = run_batched(args, dev, peak_ops)
+        if args.serve_seconds > 0:
+            served = run_served(args, dev)
     cpu = None
     if world == 1:
         sample = args.cpu_sample
@@ -334,6 +465,8 @@ def run_ours(args, world, rank, local):
         "accepted": n_accepted,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "batched": batched,
+        "served": served,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -353,6 +486,12 @@ def main():
     ap.add_argument("--chunk", type=int, default=1 << 22)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--batched-n", type=int, default=50_000_000)
+    ap.add_argument("--batched-steps", type=int, default=10, help="0 skips the batched leg")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="0 skips the served leg")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -329,6 +329,68 @@ shouji_status shouji_batch_tune(shouji_batch *batch, const uint8_t *reads,
 
 void shouji_batch_destroy(shouji_batch *batch);
 
+/*
+ * Serving loop -- filter requests as they arrive (continuous batching).
+ *
+ * The paper integrates the filter into read mappers, which produce candidate
+ * pairs continuously and keep only the pairs the filter accepts (Sec. 3.6,
+ * Table 15).  A server takes requests from any host thread.  A dispatcher
+ * thread admits them in arrival order into slots.  A slot is a batch object
+ * (one CUDA graph) with its own stream and device buffers.  An admitted
+ * request is copied in, filtered and copied out on its slot's stream, so
+ * requests admitted while others are on the GPU run concurrently with them;
+ * a finished slot takes the next queued request at once.
+ *
+ * shouji_server_create makes slots on the current device until the next
+ * one would exceed memory_budget bytes (the first slot measures the cost of
+ * one) or max_slots exist, then starts the dispatcher.
+ *   max_request_pairs  largest request; max_m, e_min, e_max, with_n,
+ *                      tune_cache: as shouji_batch_create.
+ *   max_stride         largest row stride of a request (>= max_m).
+ * Errors: SHOUJI_EINVAL; SHOUJI_ENOMEM (not even one slot fits the budget
+ * or the device); SHOUJI_ECUDA.
+ *
+ * shouji_server_info: number of slots and device bytes of one slot.
+ *
+ * shouji_server_submit queues one request and returns at once with its id.
+ * Host buffers, as shouji_batch_run's device ones (reads/refs rows of
+ * `stride` bytes, lens, E_per_pair, accept, optional count), must stay
+ * valid and untouched until shouji_server_wait returns for the id.  Pinned
+ * host buffers let the copies run asynchronously.
+ * Errors: SHOUJI_EINVAL (bad argument or the server is stopping).
+ *
+ * shouji_server_wait blocks until the request is done or timeout_s seconds
+ * have passed (SHOUJI_ETIMEOUT; the request stays queued or in flight and
+ * can be waited for again).  On completion it writes the latency, from
+ * submit to completion in seconds, into latency_s (when not NULL), forgets
+ * the id, and returns the request's status.
+ *
+ * shouji_server_destroy finishes every queued and in-flight request, stops
+ * the dispatcher and frees everything.
+ */
+typedef struct shouji_server shouji_server;
+
+shouji_status shouji_server_create(size_t max_request_pairs, uint32_t max_m,
+                                   uint64_t max_stride, int e_min, int e_max,
+                                   int with_n, size_t memory_budget,
+                                   int max_slots, const char *tune_cache,
+                                   shouji_server **out);
+
+shouji_status shouji_server_info(shouji_server *server, int *slots,
+                                 uint64_t *bytes_per_slot);
+
+shouji_status shouji_server_submit(shouji_server *server, const uint8_t *reads,
+                                   const uint8_t *refs, uint64_t stride,
+                                   const uint16_t *lens,
+                                   const uint8_t *E_per_pair, size_t n_pairs,
+                                   uint32_t *accept, uint8_t *count,
+                                   uint64_t *request_id);
+
+shouji_status shouji_server_wait(shouji_server *server, uint64_t request_id,
+                                 double timeout_s, double *latency_s);
+
+void shouji_server_destroy(shouji_server *server);
+
 #ifdef __cplusplus
 }
 #endif

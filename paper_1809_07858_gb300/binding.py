@@ -25,7 +25,7 @@ __all__ = [
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
-    "Batch",
+    "Batch", "Server",
 ]
 
 _lib = None
@@ -78,6 +78,19 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_batch_tune.restype = ctypes.c_int
     lib.shouji_batch_destroy.argtypes = [vp]
     lib.shouji_batch_destroy.restype = None
+    lib.shouji_server_create.argtypes = [sz, u32, u64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         sz, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(vp)]
+    lib.shouji_server_create.restype = ctypes.c_int
+    lib.shouji_server_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    lib.shouji_server_info.restype = ctypes.c_int
+    lib.shouji_server_submit.argtypes = [vp, vp, vp, u64, vp, vp, sz, vp, vp,
+                                         ctypes.POINTER(ctypes.c_uint64)]
+    lib.shouji_server_submit.restype = ctypes.c_int
+    lib.shouji_server_wait.argtypes = [vp, u64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.shouji_server_wait.restype = ctypes.c_int
+    lib.shouji_server_destroy.argtypes = [vp]
+    lib.shouji_server_destroy.restype = None
     lib.shouji_pipeline_create.argtypes = [u32, sz, sz, ctypes.c_int, ctypes.POINTER(vp)]
     lib.shouji_pipeline_create.restype = ctypes.c_int
     lib.shouji_pipeline_run.argtypes = [vp, vp, vp, u64, sz, ctypes.c_int, vp, vp, vp,
@@ -355,6 +368,71 @@ class Batch:
         if getattr(self, "_h", None) is not None and self._h.value:
             load_library().shouji_batch_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """``shouji_server_*``: requests of mixed lengths and thresholds filtered as
+    they arrive, with continuous batching over memory-budgeted slots.
+
+    Buffers are numpy arrays or CPU torch tensors (pinned for overlap) and must
+    stay alive until ``wait`` returns for the request.
+    """
+
+    def __init__(self, max_request_pairs: int, max_m: int, e_min: int, e_max: int, *,
+                 max_stride: int | None = None, with_n: bool = False,
+                 memory_budget: int = 40 << 30, max_slots: int = 8,
+                 tune_cache: str | None = None):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.shouji_server_create(max_request_pairs, max_m,
+                                        max_m if max_stride is None else max_stride, e_min,
+                                        e_max, int(with_n), memory_budget, max_slots,
+                                        tune_cache.encode() if tune_cache else None,
+                                        ctypes.byref(h)), "shouji_server_create")
+        self._h = h
+        self._keep = {}
+
+    def info(self):
+        slots = ctypes.c_int(0)
+        bps = ctypes.c_uint64(0)
+        _check(load_library().shouji_server_info(self._h, ctypes.byref(slots), ctypes.byref(bps)),
+               "shouji_server_info")
+        return slots.value, bps.value
+
+    def submit(self, reads, refs, lens, E_per_pair, accept, count=None, *, n_pairs=None,
+               stride=None) -> int:
+        n = len(lens) if n_pairs is None else n_pairs
+        stride = reads.shape[1] if stride is None else stride
+        rid = ctypes.c_uint64(0)
+        _check(load_library().shouji_server_submit(
+            self._h, _host_ptr(reads), _host_ptr(refs), stride, _host_ptr(lens),
+            _host_ptr(E_per_pair), n, _host_ptr(accept), _host_ptr(count), ctypes.byref(rid)),
+            "shouji_server_submit")
+        self._keep[rid.value] = (reads, refs, lens, E_per_pair, accept, count)
+        return rid.value
+
+    def wait(self, request_id: int, timeout: float = 60.0) -> float:
+        """Block until done; returns the latency in seconds.  Raises
+        ``ShoujiError`` with status 4 (SHOUJI_ETIMEOUT) when the deadline passes."""
+        lat = ctypes.c_double(0.0)
+        st = load_library().shouji_server_wait(self._h, request_id, float(timeout),
+                                               ctypes.byref(lat))
+        if st != 4:
+            self._keep.pop(request_id, None)
+        _check(st, "shouji_server_wait")
+        return lat.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().shouji_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
 
     def __del__(self):
         try:
