@@ -40,7 +40,7 @@ ALU_LANES_PER_SM_CLK = 64   # LOP3/SHF/PRMT issue rate of the integer ALU pipe p
 # from one ncu capture, keyed by the hash of the filter kernel source it was
 # taken on; scaled to a 30M-pair launch.  Reported as null once the kernel
 # source changes.
-FILTER_TRAFFIC = {"7ee2de732f26b06e": 1.542e9}  # profiles/filter_kernel_E5_m100.md
+FILTER_TRAFFIC = {"0325f129af588db8": 1.540e9}  # profiles/filter_kernel_E5_m100.md
 
 
 def alu_ops_per_pair(m: int, E: int) -> float:

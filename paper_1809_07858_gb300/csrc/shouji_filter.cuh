@@ -201,9 +201,16 @@ struct View {
 // Keeping them in registers saves 3 of every U+3 map evaluations; for large
 // E the 3(2E+1) extra live registers cost more than they save, and the
 // shared columns are recomputed instead.
+#ifndef SHOUJI_CARRY_MAX_E
+#define SHOUJI_CARRY_MAX_E 15
+#endif
+#ifndef SHOUJI_LARGE_E_MIN_BLOCKS
+#define SHOUJI_LARGE_E_MIN_BLOCKS 1
+#endif
+
 template <int E>
 struct Carry {
-    static constexpr bool kOn = E <= 8;
+    static constexpr bool kOn = E <= SHOUJI_CARRY_MAX_E;
     uint32_t M[kOn ? 2 * E + 1 : 1][3];
 };
 
@@ -211,10 +218,11 @@ struct Carry {
 //   BOUNDS: columns and read positions may fall outside [0, m) (edge chunks);
 //           an unbounded chunk needs every column it evaluates and every read
 //           position those columns touch inside [0, m).
-//   MASKS:  N masks and/or per-pair thresholds are present.
+//   MASKS:  0 none; 1 N masks (of reads and refs); 2 N masks that may be
+//           absent and per-pair thresholds.
 // With a carry, the chunk evaluates the U columns c0+3..c0+U+2 and takes
 // c0..c0+2 from the carry; without, it evaluates all U+3 columns c0..c0+U+2.
-template <int E, int U, bool BOUNDS, bool MASKS>
+template <int E, int U, bool BOUNDS, int MASKS>
 __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[E + 1], int c0,
                                       Carry<E> &carry, uint32_t &s0, uint32_t &s1, uint32_t &s2,
                                       uint32_t (&C)[8])
@@ -225,6 +233,8 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
     constexpr int NR = NC + 2 * E;      // read positions c0+K0-E .. c0+U+2+E
     uint32_t th[NC], tl[NC], tx[MASKS ? NC : 1];
     uint32_t rh[NR], rl[NR], rx[MASKS ? NR : 1];
+    // level 1 always has both N masks; level 2 may have none
+    const bool nm = MASKS == 1 || (MASKS == 2 && v.rfn != nullptr);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
         const int p = c0 + K0 + k;
@@ -232,8 +242,8 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
         const uint2 w = ok ? __ldg(v.rf + (size_t)p * 32) : make_uint2(0u, 0u);
         th[k] = w.x;
         tl[k] = w.y;
-        if constexpr (MASKS)
-            tx[k] = (ok && v.rfn) ? __ldg(v.rfn + (size_t)p * 32) : 0u;
+        if constexpr (MASKS != 0)
+            tx[k] = (ok && nm) ? __ldg(v.rfn + (size_t)p * 32) : 0u;
     }
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
@@ -242,16 +252,18 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
         const uint2 w = ok ? __ldg(v.rd + (size_t)q * 32) : make_uint2(0u, 0u);
         rh[i] = w.x;
         rl[i] = w.y;
-        if constexpr (MASKS)
-            rx[i] = (ok && v.rdn) ? __ldg(v.rdn + (size_t)q * 32) : 0u;
+        if constexpr (MASKS != 0)
+            rx[i] = (ok && nm) ? __ldg(v.rdn + (size_t)q * 32) : 0u;
     }
 
     // Mismatch bits of diagonal d at evaluated column k (column c0+K0+k).
     auto column = [&](int d, int k) -> uint32_t {
         const int i = k - d + E;
         uint32_t x = (th[k] ^ rh[i]) | (tl[k] ^ rl[i]);
-        if constexpr (MASKS)
-            x |= tx[k] | rx[i] | inactive[d < 0 ? -d : d];
+        if constexpr (MASKS != 0)
+            x |= tx[k] | rx[i];
+        if constexpr (MASKS == 2)
+            x |= inactive[d < 0 ? -d : d];
         if constexpr (BOUNDS) {
             const int p = c0 + K0 + k, q = p - d;
             if (p >= v.m || q < 0 || q >= v.m)
@@ -345,7 +357,7 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
 }
 
 // Columns 0..2 of every diagonal: the carry the first chunk starts from.
-template <int E, bool MASKS>
+template <int E, int MASKS>
 __device__ __forceinline__ void carry_prologue(const View &v, const uint32_t (&inactive)[E + 1],
                                                Carry<E> &carry)
 {
@@ -360,11 +372,12 @@ __device__ __forceinline__ void carry_prologue(const View &v, const uint32_t (&i
                     const uint2 t = __ldg(v.rf + (size_t)p * 32);
                     const uint2 r = __ldg(v.rd + (size_t)q * 32);
                     x = (t.x ^ r.x) | (t.y ^ r.y);
-                    if constexpr (MASKS) {
+                    if constexpr (MASKS != 0) {
                         if (v.rfn)
                             x |= __ldg(v.rfn + (size_t)p * 32) | __ldg(v.rdn + (size_t)q * 32);
-                        x |= inactive[d < 0 ? -d : d];
                     }
+                    if constexpr (MASKS == 2)
+                        x |= inactive[d < 0 ? -d : d];
                 }
                 carry.M[d + E][p] = x;
             }
@@ -374,7 +387,7 @@ __device__ __forceinline__ void carry_prologue(const View &v, const uint32_t (&i
 
 // The whole filter for one group of 32 pairs: every window of the group's
 // m columns; C receives the bit-sliced 8-bit counts of ones.
-template <int E, int U, bool MASKS>
+template <int E, int U, int MASKS>
 __device__ __forceinline__ void filter_group(const View &v, const uint32_t (&inactive)[E + 1],
                                              uint32_t (&C)[8])
 {
@@ -387,21 +400,21 @@ __device__ __forceinline__ void filter_group(const View &v, const uint32_t (&ina
     Carry<E> carry;
     carry_prologue<E, MASKS>(v, inactive, carry);
     constexpr int K0 = Carry<E>::kOn ? 3 : 0;
-    if constexpr (MASKS) {
-        for (int c0 = 0; c0 < m; c0 += U)
-            chunk<E, U, true, true>(v, inactive, c0, carry, s0, s1, s2, C);
-    } else {
-        for (int c0 = 0; c0 < m; c0 += U) {
-            if ((c0 + K0 - E >= 0) && (c0 + U + 2 + E < m))
-                chunk<E, U, false, false>(v, inactive, c0, carry, s0, s1, s2, C);
-            else
-                chunk<E, U, true, false>(v, inactive, c0, carry, s0, s1, s2, C);
-        }
+    for (int c0 = 0; c0 < m; c0 += U) {
+        if ((c0 + K0 - E >= 0) && (c0 + U + 2 + E < m))
+            chunk<E, U, false, MASKS>(v, inactive, c0, carry, s0, s1, s2, C);
+        else
+            chunk<E, U, true, MASKS>(v, inactive, c0, carry, s0, s1, s2, C);
     }
 }
 
-template <int E, int U, bool MASKS>
-__global__ void __launch_bounds__(kThreads)
+// Minimum resident CTAs per SM requested from ptxas (caps registers) for
+// thresholds above 8.
+template <int E>
+constexpr int min_blocks() { return E > 8 ? SHOUJI_LARGE_E_MIN_BLOCKS : 1; }
+
+template <int E, int U, int MASKS>
+__global__ void __launch_bounds__(kThreads, min_blocks<E>())
 filter_kernel(FilterArgs a)
 {
     const size_t g = (size_t)blockIdx.x * kThreads + threadIdx.x;  // group of 32 pairs
@@ -429,7 +442,7 @@ filter_kernel(FilterArgs a)
 #pragma unroll
     for (int j = 0; j <= E; ++j)
         inactive[j] = 0u;
-    if (MASKS && a.E_per_pair) {
+    if (MASKS == 2 && a.E_per_pair) {
         for (int b = 0; b < 32 && (size_t)b < left; ++b) {
             const int e = a.E_per_pair[first + b];
 #pragma unroll
@@ -445,7 +458,7 @@ filter_kernel(FilterArgs a)
     uint32_t cw[8];
     counts_to_bytes(C, cw);
     uint32_t acc = le_const<E>(C);
-    if (MASKS && a.E_per_pair) {
+    if (MASKS == 2 && a.E_per_pair) {
         acc = 0u;
         for (int b = 0; b < 32 && (size_t)b < left; ++b) {
             const uint32_t cnt = (cw[b >> 2] >> (8 * (b & 3))) & 0xFFu;
@@ -474,10 +487,12 @@ cudaError_t launch_E(const FilterArgs &a, cudaStream_t s)
     constexpr int U = SHOUJI_FILTER_U;
     const size_t groups = groups_of(a.n_pairs);
     const size_t blocks = (groups + kThreads - 1) / kThreads;
-    if (a.reads_n || a.E_per_pair)
-        filter_kernel<E, U, true><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    if (a.E_per_pair)
+        filter_kernel<E, U, 2><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    else if (a.reads_n)
+        filter_kernel<E, U, 1><<<(unsigned)blocks, kThreads, 0, s>>>(a);
     else
-        filter_kernel<E, U, false><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+        filter_kernel<E, U, 0><<<(unsigned)blocks, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -489,118 +504,4 @@ cudaError_t launch_filter_E(const FilterArgs &a, cudaStream_t s)
     return filt::launch_E<E>(a, s);
 }
 
-}  // namespace shouji
-
-// ---------------------------------------------------------------------------
-// Persistent filter of one threshold class of a bucketed batch.
-#include "shouji_batch.cuh"
-
-namespace shouji {
-namespace batch {
-
-template <int E, bool WITH_N>
-__global__ void __launch_bounds__(filt::kThreads)
-batch_filter_kernel(FilterParams p)
-{
-    const Tables *T = p.tables;
-    const uint32_t G = T->ec_groups[E];
-    if (G == 0)
-        return;
-    const uint32_t first = T->ec_first[E];
-    const uint32_t nb = T->ec_count[E];
-    // this threshold's buckets, cached in shared memory (at most 255)
-    __shared__ uint32_t s_gstart[kMaxM], s_m[kMaxM], s_slot[kMaxM], s_rel0[kMaxM];
-    __shared__ uint64_t s_poff[kMaxM];
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
-        const uint32_t b = first + i, mc = T->bk_mc[b];
-        s_gstart[i] = T->bk_gstart[b];
-        s_m[i] = T->bk_m[b];
-        s_slot[i] = T->bk_slot[b];
-        s_rel0[i] = T->bk_slot[b] - T->mc_slot[mc];   // bucket start inside its m-class
-        s_poff[i] = T->mc_poff[mc];
-    }
-    __syncthreads();
-    // group g -> (m, first slot, packed base) of its bucket
-    auto locate = [&](uint32_t g, int &m, uint32_t &slot0, size_t &base) {
-        uint32_t lo = 0, hi = nb;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (s_gstart[mid] <= g)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        m = (int)s_m[lo];
-        const uint32_t off = 32u * (g - s_gstart[lo]);
-        slot0 = s_slot[lo] + off;
-        const uint32_t rel = s_rel0[lo] + off;
-        base = s_poff[lo] + (size_t)(rel / kTile) * m * kLanes + (rel % kTile) / 32;
-    };
-    auto run_group = [&](uint32_t g) {
-        int m;
-        uint32_t slot0;
-        size_t base;
-        locate(g, m, slot0, base);
-        filt::View v;
-        v.rd = p.preads + base;
-        v.rf = p.prefs + base;
-        v.rdn = WITH_N ? p.nreads + base : nullptr;
-        v.rfn = WITH_N ? p.nrefs + base : nullptr;
-        v.vec = nullptr;
-        v.m = m;
-        uint32_t inactive[E + 1];
-#pragma unroll
-        for (int j = 0; j <= E; ++j)
-            inactive[j] = 0u;
-        uint32_t C[8];
-        filt::filter_group<E, SHOUJI_FILTER_U, WITH_N>(v, inactive, C);
-        uint32_t cw[8];
-        filt::counts_to_bytes(C, cw);
-        uint4 *dst = reinterpret_cast<uint4 *>(p.count_slot + slot0);
-        dst[0] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
-        dst[1] = make_uint4(cw[4], cw[5], cw[6], cw[7]);
-    };
-    if (p.schedule == 2) {
-        __shared__ uint32_t s_base;
-        for (;;) {
-            if (threadIdx.x == 0)
-                s_base = atomicAdd(&p.work[E], blockDim.x);
-            __syncthreads();
-            const uint32_t base = s_base;
-            __syncthreads();
-            if (base >= G)
-                break;
-            if (base + threadIdx.x < G)
-                run_group(base + threadIdx.x);
-        }
-        return;
-    }
-    uint32_t g, gend, gstep;
-    if (p.schedule == 0) {
-        g = blockIdx.x * blockDim.x + threadIdx.x;
-        gstep = gridDim.x * blockDim.x;
-        gend = G;
-    } else {
-        // a contiguous, block-aligned range of groups per CTA
-        const uint32_t per = (G + gridDim.x - 1) / gridDim.x;
-        const uint32_t per_r = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
-        g = blockIdx.x * per_r + threadIdx.x;
-        gend = min(G, (blockIdx.x + 1) * per_r);
-        gstep = blockDim.x;
-    }
-    for (; g < gend; g += gstep)
-        run_group(g);
-}
-
-template <int E>
-cudaError_t launch_filter_E(const FilterParams &p, int threads, int ctas, cudaStream_t s)
-{
-    if (p.nreads)
-        batch_filter_kernel<E, true><<<ctas, threads, 0, s>>>(p);
-    else
-        batch_filter_kernel<E, false><<<ctas, threads, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-}  // namespace batch
 }  // namespace shouji
