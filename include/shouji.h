@@ -146,6 +146,43 @@ shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
                             uint32_t *out_vectors, void *stream);
 
 /*
+ * shouji_count -- local and semi-global ("glocal") counting.
+ *
+ * The paper counts every one of the Shouji bit-vector for end-to-end
+ * (global) alignment and leaves out the runs of ones at both ends for local
+ * alignment, or at one end for glocal alignment (Sec. 2.2.3; Supplementary
+ * Sec. 8, Fig. 6(c), where a 68-base read is filtered against a 100-base
+ * reference).  This call recounts Shouji bit-vectors written by
+ * shouji_filter (out_vectors) under a count mode:
+ *   SHOUJI_COUNT_GLOBAL        every one (the count of shouji_filter);
+ *   SHOUJI_COUNT_LOCAL         not the runs of ones at the two ends;
+ *   SHOUJI_COUNT_GLOCAL_START  not the run of ones at the start;
+ *   SHOUJI_COUNT_GLOCAL_END    not the run of ones at the end.
+ * A vector with no zero counts m in every mode.  A read shorter than its
+ * reference is filtered by packing it padded with 'N' to the reference
+ * length, with N masks: an 'N' matches nothing, like the cells past the end
+ * of the read in the paper's map.
+ *
+ *   vectors      device, bit-sliced Shouji bit-vectors of n_pairs pairs of
+ *                length m (out_vectors of shouji_filter).
+ *   E, E_per_pair as shouji_filter (the accept threshold).
+ *   mode         one of the four modes above.
+ *   out_accept   device uint32[ceil(n_pairs / 32)]: count <= E.
+ *   out_count    device uint8[n_pairs] or NULL: the count under the mode.
+ * Errors: SHOUJI_EINVAL for NULL vectors/out_accept (with n_pairs > 0), m, E
+ * or mode out of range; SHOUJI_ECUDA on a launch failure.
+ */
+#define SHOUJI_COUNT_GLOBAL 0
+#define SHOUJI_COUNT_LOCAL 1
+#define SHOUJI_COUNT_GLOCAL_START 2
+#define SHOUJI_COUNT_GLOCAL_END 3
+
+shouji_status shouji_count(const uint32_t *vectors, uint32_t m, size_t n_pairs,
+                           int E, const uint8_t *E_per_pair, int mode,
+                           uint32_t *out_accept, uint8_t *out_count,
+                           void *stream);
+
+/*
  * shouji_compact_workspace_size -- bytes of device workspace that
  * shouji_compact needs for n_pairs pairs (0 for n_pairs = 0).
  */

@@ -64,6 +64,11 @@ def _load():
                                             ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_int]
         lib.oracle_shouji_batch.restype = ctypes.c_int
+        lib.oracle_count_mode.argtypes = [u8p, ctypes.c_int, ctypes.c_int]
+        lib.oracle_count_mode.restype = ctypes.c_int
+        lib.oracle_shouji_mode.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, u8p]
+        lib.oracle_shouji_mode.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -98,6 +103,32 @@ def shouji(P, T, E: int):
     if ones < 0:
         raise MemoryError("oracle_shouji failed")
     return S, ones, ones <= E
+
+
+GLOBAL, LOCAL, GLOCAL_START, GLOCAL_END = 0, 1, 2, 3
+
+
+def count_mode(S, mode: int) -> int:
+    """Ones of a Shouji bit-vector under a count mode (Sec. 2.2.3, Supp. Sec. 8):
+    0 all, 1 not the runs at both ends, 2 not the leading run, 3 not the
+    trailing run; a vector with no zero counts its length (reading R10)."""
+    S = np.ascontiguousarray(S, dtype=np.uint8)
+    return _load().oracle_count_mode(S.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), len(S),
+                                     mode)
+
+
+def shouji_mode(P, T, E: int, mode: int):
+    """The filter for a pattern P no longer than the text T (P past its end
+    reads as out of the band) with a count mode.  Returns (vector, count)."""
+    P, T = _as_bytes(P), _as_bytes(T)
+    m = len(T)
+    assert len(P) <= m and m > 0
+    S = np.zeros(m, dtype=np.uint8)
+    c = _load().oracle_shouji_mode(P, len(P), T, m, E, mode,
+                                   S.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    if c < 0:
+        raise ValueError("oracle_shouji_mode: bad argument")
+    return S, c
 
 
 def edit_distance(a, b) -> int:

@@ -41,6 +41,9 @@
  *       i.e. CZ(Shouji) >= m - E (Sec. 2.2.3, Algorithm 1, step 3).
  *   R8  The base 'N' matches nothing, not even another 'N' (the paper is
  *       silent on ambiguous bases).
+ *   R10 Local / glocal counting drops the runs of ones at the ends of the
+ *       Shouji bit-vector; a vector with no zero counts m.  A pattern
+ *       shorter than the text reads as out of the band past its end.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -53,14 +56,14 @@
 /* ---------------------------------------------------------------------- */
 static int is_unknown_base(char x) { return x == 'N'; }
 
-void oracle_neighborhood_map(const char *P, const char *T, int m, int E,
-                             uint8_t *map)
+static void build_map(const char *P, int mp, const char *T, int m, int E,
+                      uint8_t *map)
 {
     for (int d = -E; d <= E; ++d) {
         for (int c = 0; c < m; ++c) {
             int i = c - d;               /* index into P (row of N) */
             uint8_t cell;
-            if (i < 0 || i >= m)
+            if (i < 0 || i >= mp)
                 cell = 1;                /* R3: outside the band */
             else if (is_unknown_base(P[i]) || is_unknown_base(T[c]))
                 cell = 1;                /* R8 */
@@ -69,6 +72,12 @@ void oracle_neighborhood_map(const char *P, const char *T, int m, int E,
             map[(size_t)(d + E) * m + c] = cell;
         }
     }
+}
+
+void oracle_neighborhood_map(const char *P, const char *T, int m, int E,
+                             uint8_t *map)
+{
+    build_map(P, m, T, m, E, map);
 }
 
 /* Algorithm 2: CZ counts the zeros of a bit-vector. */
@@ -90,26 +99,18 @@ static void segment(const uint8_t *map, int m, int E, int d, int c,
         seg[k] = (c + k < m) ? map[(size_t)(d + E) * m + c + k] : 1;
 }
 
-/* ---------------------------------------------------------------------- */
-/* Steps 1-3 for one pair.  Writes the Shouji bit-vector (m bytes, 0/1) to */
-/* S when S is not NULL and returns the number of ones in it (the edit     */
-/* estimate); the pair is accepted iff the return value is <= E.           */
-/* Returns -1 on an allocation failure or a bad argument.                  */
-/* ---------------------------------------------------------------------- */
-int oracle_shouji(const char *P, const char *T, int m, int E, uint8_t *S)
+/* Steps 1 and 2 for a pattern P of length mp against a text T of length m
+ * (mp = m in the global mode of the paper; a shorter P reads as out of the
+ * band past its end, as the dashes of Fig. 6(c)).  Fills shouji[0..m). */
+static int shouji_vector(const char *P, int mp, const char *T, int m, int E,
+                         uint8_t *shouji)
 {
-    if (m <= 0 || E < 0)
-        return -1;
     uint8_t *map = (uint8_t *)malloc((size_t)(2 * E + 1) * m);
-    uint8_t *shouji = (uint8_t *)malloc((size_t)m);
-    if (!map || !shouji) {
-        free(map);
-        free(shouji);
+    if (!map)
         return -1;
-    }
 
     /* Step 1 */
-    oracle_neighborhood_map(P, T, m, E, map);
+    build_map(P, mp, T, m, E, map);
 
     /* Step 2: the Shouji bit-vector starts as all ones. */
     for (int c = 0; c < m; ++c)
@@ -148,13 +149,82 @@ int oracle_shouji(const char *P, const char *T, int m, int E, uint8_t *S)
                     shouji[c + k] = Z[k];
     }
 
+    free(map);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Steps 1-3 for one pair.  Writes the Shouji bit-vector (m bytes, 0/1) to */
+/* S when S is not NULL and returns the number of ones in it (the edit     */
+/* estimate); the pair is accepted iff the return value is <= E.           */
+/* Returns -1 on an allocation failure or a bad argument.                  */
+/* ---------------------------------------------------------------------- */
+int oracle_shouji(const char *P, const char *T, int m, int E, uint8_t *S)
+{
+    if (m <= 0 || E < 0)
+        return -1;
+    uint8_t *shouji = (uint8_t *)malloc((size_t)m);
+    if (!shouji || shouji_vector(P, m, T, m, E, shouji) != 0) {
+        free(shouji);
+        return -1;
+    }
     /* Step 3 (Sec. 2.2.3): count the ones. */
     int ones = m - CZ(shouji, m);
     if (S)
         memcpy(S, shouji, (size_t)m);
-    free(map);
     free(shouji);
     return ones;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Local and semi-global ("glocal") counting (Sec. 2.2.3; Supplementary    */
+/* Sec. 8, Fig. 6(c)): the ones of the Shouji bit-vector that lie in the   */
+/* run at one or both of its ends are not counted.                         */
+/*   mode 0 global: every one;                                             */
+/*   mode 1 local: not the leading nor the trailing run of ones;           */
+/*   mode 2 glocal: not the leading run; mode 3 glocal: not the trailing.  */
+/* Reading R10: a vector without any zero has no end runs to drop (all of  */
+/* it is mismatch) and counts m.                                           */
+/* ---------------------------------------------------------------------- */
+int oracle_count_mode(const uint8_t *S, int m, int mode)
+{
+    int first = -1, last = -1;
+    for (int c = 0; c < m; ++c) {
+        if (S[c] == 0) {
+            if (first < 0)
+                first = c;
+            last = c;
+        }
+    }
+    if (first < 0)
+        return m;
+    int lo = (mode == 1 || mode == 2) ? first : 0;
+    int hi = (mode == 1 || mode == 3) ? last : m - 1;
+    int ones = 0;
+    for (int c = lo; c <= hi; ++c)
+        if (S[c] == 1)
+            ones = ones + 1;
+    return ones;
+}
+
+/* The filter for a pattern P of length mp <= m against a text T of length
+ * m, with the count mode above; S (m bytes) may be NULL.  Returns the
+ * count, or -1 on a bad argument or an allocation failure. */
+int oracle_shouji_mode(const char *P, int mp, const char *T, int m, int E,
+                       int mode, uint8_t *S)
+{
+    if (m <= 0 || mp < 0 || mp > m || E < 0 || mode < 0 || mode > 3)
+        return -1;
+    uint8_t *shouji = (uint8_t *)malloc((size_t)m);
+    if (!shouji || shouji_vector(P, mp, T, m, E, shouji) != 0) {
+        free(shouji);
+        return -1;
+    }
+    int count = oracle_count_mode(shouji, m, mode);
+    if (S)
+        memcpy(S, shouji, (size_t)m);
+    free(shouji);
+    return count;
 }
 
 /* ---------------------------------------------------------------------- */

@@ -25,8 +25,11 @@ __all__ = [
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
-    "Batch", "Server",
+    "Batch", "Server", "shouji_count", "COUNT_GLOBAL", "COUNT_LOCAL", "COUNT_GLOCAL_START",
+    "COUNT_GLOCAL_END",
 ]
+
+COUNT_GLOBAL, COUNT_LOCAL, COUNT_GLOCAL_START, COUNT_GLOCAL_END = 0, 1, 2, 3
 
 _lib = None
 
@@ -91,6 +94,8 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_server_wait.restype = ctypes.c_int
     lib.shouji_server_destroy.argtypes = [vp]
     lib.shouji_server_destroy.restype = None
+    lib.shouji_count.argtypes = [vp, u32, sz, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
+    lib.shouji_count.restype = ctypes.c_int
     lib.shouji_pipeline_create.argtypes = [u32, sz, sz, ctypes.c_int, ctypes.POINTER(vp)]
     lib.shouji_pipeline_create.restype = ctypes.c_int
     lib.shouji_pipeline_run.argtypes = [vp, vp, vp, u64, sz, ctypes.c_int, vp, vp, vp,
@@ -192,6 +197,22 @@ def shouji_filter(reads, refs, m: int, n_pairs: int, E: int, *, reads_nmask=None
                              _ptr(out_count), _ptr(out_vectors), _stream(stream)),
            "shouji_filter")
     return out_accept, out_count, out_vectors
+
+
+def shouji_count(vectors, m: int, n_pairs: int, E: int, mode: int, *, E_per_pair=None,
+                 out_accept=None, out_count=None, count: bool = True, stream=None):
+    """Recount Shouji bit-vectors (from ``shouji_filter(..., vectors=True)``)
+    under a count mode.  Returns ``(accept_words, count)``."""
+    torch = _torch()
+    dev = vectors.device
+    if out_accept is None:
+        out_accept = torch.empty(max(1, (n_pairs + 31) // 32), dtype=torch.int32, device=dev)
+    if out_count is None and count:
+        out_count = torch.empty(max(1, n_pairs), dtype=torch.uint8, device=dev)
+    _check(load_library().shouji_count(_ptr(vectors), m, n_pairs, E, _ptr(E_per_pair), mode,
+                                       _ptr(out_accept), _ptr(out_count), _stream(stream)),
+           "shouji_count")
+    return out_accept, out_count
 
 
 def shouji_compact_workspace_size(n_pairs: int) -> int:

@@ -23,8 +23,8 @@ MUTANTS = {
     "main_wins_ties": [("if (CZ(cand, 4) > CZ(Z, 4))\n                memcpy",
                         "if (CZ(cand, 4) >= CZ(Z, 4))\n                memcpy")],
     "upper_before_lower": [("int d = (side == 0) ? -j : +j;", "int d = (side == 0) ? +j : -j;")],
-    "P_and_T_exchanged": [("oracle_neighborhood_map(P, T, m, E, map);",
-                           "oracle_neighborhood_map(T, P, m, E, map);")],
+    "P_and_T_exchanged": [("build_map(P, mp, T, m, E, map);",
+                           "build_map(T, mp, P, m, E, map);")],
     "main_diagonal_dropped": [("if (CZ(cand, 4) > CZ(Z, 4))\n                memcpy(Z, cand, 4);\n        }",
                                "if (0)\n                memcpy(Z, cand, 4);\n        }")],
     "past_end_segment_is_match": [("seg[k] = (c + k < m) ? map[(size_t)(d + E) * m + c + k] : 1;",

@@ -154,3 +154,52 @@ def test_false_accept_reject_report_tiny_brute_force(capsys):
         print("m=4 E=%d pairs=%d similar=%d FA=%d FR=%d" % (E, len(ed), int((ed <= E).sum()), fa, fr))
         if E == 0:
             assert fa == 0 and fr == 0
+
+
+# ------------------------------------------------------------ count modes (N3)
+def test_count_modes_hand_worked():
+    """Sec. 2.2.3 / Supp. Sec. 8: local counting leaves out the runs of ones at
+    both ends of the Shouji bit-vector, glocal the run at one end.  Worked by
+    hand: 11010011 has ones at 0,1,3,6,7; first zero 2, last zero 5."""
+    S = [1, 1, 0, 1, 0, 0, 1, 1]
+    assert oracle.count_mode(S, oracle.GLOBAL) == 5
+    assert oracle.count_mode(S, oracle.LOCAL) == 1          # only column 3
+    assert oracle.count_mode(S, oracle.GLOCAL_START) == 3   # columns 3, 6, 7
+    assert oracle.count_mode(S, oracle.GLOCAL_END) == 3     # columns 0, 1, 3
+    for mode in range(4):
+        assert oracle.count_mode([1, 1, 1, 1], mode) == 4   # reading R10: no zero counts m
+        assert oracle.count_mode([0, 0, 0], mode) == 0
+        assert oracle.count_mode([0, 1, 1, 0], mode) == 2
+    assert [oracle.count_mode([1, 0, 0, 0], k) for k in range(4)] == [1, 0, 0, 1]
+
+
+def test_short_pattern_is_out_of_band_past_its_end():
+    """A pattern shorter than the text reads as out of the band past its end
+    (the dashes of Fig. 6(c)); that is the same as padding it with 'N', which
+    matches nothing (R8) -- the equivalence the GPU path relies on."""
+    rng = random.Random(21)
+    for _ in range(200):
+        m = rng.randint(4, 60)
+        mp = rng.randint(0, m)
+        E = rng.randint(0, 5)
+        T = "".join(rng.choice("ACGT") for _ in range(m))
+        P = "".join(rng.choice("ACGT") for _ in range(mp))
+        for mode in range(4):
+            S1, c1 = oracle.shouji_mode(P, T, E, mode)
+            S2, c2 = oracle.shouji_mode(P + "N" * (m - mp), T, E, mode)
+            assert (S1 == S2).all() and c1 == c2
+        S3, ones, _ = oracle.shouji(P + "N" * (m - mp), T, E)
+        assert (S3 == S1).all() and ones == oracle.count_mode(S1, oracle.GLOBAL)
+
+
+def test_fig6c_local_count_parity_unpinned():
+    """Fig. 6(c) (68-base read, 100-base reference, E = 4, local): the figure
+    states 2 edits; under the readings taken here (Algorithm 1's strict
+    comparisons, lower before upper) the local count is 3, with ones at
+    columns 1, 20 and 28 inside the end runs.  Kept as a regression value."""
+    lines = [l for l in open(__import__("os").path.join(
+        __import__("os").path.dirname(__file__), "golden", "fig6c.txt")) if not l.startswith("#")]
+    d = dict(l.rstrip("\n").split(" ", 1) for l in lines if l.strip())
+    S, local = oracle.shouji_mode(d["P"], d["T"], int(d["E"]), oracle.LOCAL)
+    assert local == 3
+    assert [i for i in range(len(S)) if S[i]][:3] == [1, 20, 28]
