@@ -2,7 +2,7 @@
 
 A ctypes wrapper around ``shouji_oracle.c``: a plain, single-pair-at-a-time C
 restatement of the Shouji filter (arXiv 1809.07858, Sec. 2.2 and Algorithms
-1-2) plus the global edit distance used as ground truth for false-accept /
+1-2), of MAGNET (Supplementary Sec. 7, Algorithms 3-4), plus the global edit distance used as ground truth for false-accept /
 false-reject counts (Sec. 3.2).  Only the tests, ``__graft_entry__.smoke()``
 and the benchmark's CPU-baseline leg may import this package.  It shares no
 code with the CUDA library and never imports it.
@@ -14,6 +14,12 @@ Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``
                     Hamming reduction, identical pairs, shifted-copy closed
                     forms, tiny brute force); the one Fig. 6(a) vector is
                     "parity unpinned" (the printed vector is garbled)
+  count_mode        pinned (hand cases of the local / glocal rules); the Fig. 6(c)
+                    local count is "parity unpinned" (3 here, 2 printed)
+  magnet            pinned (Fig. 6(a),(b) printed counts, hand-traced cases per
+                    reading, E = 0 identity test, shift / substitution closed
+                    forms; tests/test_magnet_oracle.py); the Fig. 6(c) local
+                    count is "parity unpinned" (5 here, 4 printed)
   edit_distance     pinned (textbook identities and brute force on tiny inputs)
 """
 from __future__ import annotations
@@ -69,6 +75,9 @@ def _load():
         lib.oracle_shouji_mode.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, u8p]
         lib.oracle_shouji_mode.restype = ctypes.c_int
+        lib.oracle_magnet_mode.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, u8p]
+        lib.oracle_magnet_mode.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -129,6 +138,20 @@ def shouji_mode(P, T, E: int, mode: int):
     if c < 0:
         raise ValueError("oracle_shouji_mode: bad argument")
     return S, c
+
+
+def magnet(P, T, E: int, mode: int = 0):
+    """MAGNET (Supp. Sec. 7, Algorithms 3-4) for a pattern P no longer than the
+    text T, with a count mode.  Returns (MAGNET vector, count)."""
+    P, T = _as_bytes(P), _as_bytes(T)
+    m = len(T)
+    assert len(P) <= m and m > 0
+    V = np.zeros(m, dtype=np.uint8)
+    c = _load().oracle_magnet_mode(P, len(P), T, m, E, mode,
+                                   V.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    if c < 0:
+        raise ValueError("oracle_magnet_mode: bad argument")
+    return V, c
 
 
 def edit_distance(a, b) -> int:

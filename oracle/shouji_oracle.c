@@ -338,3 +338,126 @@ int oracle_shouji_batch(const char *reads, const char *refs, size_t stride,
     free(tids);
     return failed ? -1 : 0;
 }
+
+/* ====================================================================== */
+/* MAGNET (Supplementary Sec. 7, Algorithms 3 and 4): the paper's second  */
+/* filter on the same neighborhood map.  Readings (listed with evidence   */
+/* in the design notes):                                                  */
+/*   M1  As in Algorithm 1, the printed extraction loop overwrites its     */
+/*       choice for every j; the prose selects the longest of all 2E+1     */
+/*       diagonals' runs, so the choice is a running best.                 */
+/*   M2  Diagonal j's pair: the lower run wins only when strictly longer   */
+/*       (Algorithm 4 prefers the upper on ties); a pair's winner replaces */
+/*       the best so far only when strictly longer (the first j wins ties);*/
+/*       the main diagonal replaces it only when strictly longer.          */
+/*   M3  CCZ returns the longest run of consecutive zeros of a diagonal    */
+/*       inside columns [SI, EI], the leftmost of equally long runs.       */
+/*   M4  The extracted run's columns become zeros of the MAGNET vector;    */
+/*       the columns just before and after it (the encapsulation bits)     */
+/*       stay ones; subproblems cover [e+2, EI] (first) and [SI, s-2].     */
+/*   M5  The counter `calls` counts extractions in the order they happen   */
+/*       (a call that extracts nothing gives its number back); at most     */
+/*       E+1 extractions.  A range without any zero extracts nothing.      */
+/*   M6  Only the first extraction checks the length bound: a longest run  */
+/*       shorter than ceil((m-E)/(E+1)) rejects the pair at once (the      */
+/*       MAGNET vector stays all ones).                                    */
+/* ====================================================================== */
+typedef struct {
+    const uint8_t *map;
+    int m, E;
+    uint8_t *vec;
+    int rejected;
+} magnet_state;
+
+/* CCZ: longest run of zeros of diagonal d inside [SI, EI] (M3). */
+static int CCZ(const magnet_state *st, int d, int SI, int EI, int *s_out, int *e_out)
+{
+    int best = 0, bs = -1, run = 0;
+    for (int c = SI; c <= EI; ++c) {
+        if (st->map[(size_t)(d + st->E) * st->m + c] == 0) {
+            ++run;
+            if (run > best) {
+                best = run;
+                bs = c - run + 1;
+            }
+        } else {
+            run = 0;
+        }
+    }
+    *s_out = bs;
+    *e_out = bs + best - 1;
+    return best;
+}
+
+static int EXEN(magnet_state *st, int SI, int EI, int calls)
+{
+    const int E = st->E;
+    if (!(SI <= EI && calls <= E + 1))
+        return calls - 1;
+    /* Extraction (M1, M2) */
+    int len = 0, s = -1, e = -2;
+    for (int j = 1; j <= E; ++j) {
+        int s1, e1, s2, e2;
+        int X = CCZ(st, -j, SI, EI, &s1, &e1);   /* lower diagonal j */
+        int Y = CCZ(st, +j, SI, EI, &s2, &e2);   /* upper diagonal j */
+        int L = X > Y ? X : Y;
+        int ls = X > Y ? s1 : s2, le = X > Y ? e1 : e2;
+        if (L > len) {
+            len = L;
+            s = ls;
+            e = le;
+        }
+    }
+    {
+        int s1, e1;
+        int X = CCZ(st, 0, SI, EI, &s1, &e1);   /* main diagonal */
+        if (X > len) {
+            len = X;
+            s = s1;
+            e = e1;
+        }
+    }
+    if (len == 0)
+        return calls - 1;                         /* nothing to extract (M5) */
+    /* Early termination, first call only (M6) */
+    if (calls == 1 && len < (st->m - E + E) / (E + 1)) {  /* ceil((m-E)/(E+1)) */
+        st->rejected = 1;
+        return 0;
+    }
+    for (int c = s; c <= e; ++c)
+        st->vec[c] = 0;                           /* M4 */
+    calls = EXEN(st, e + 2, EI, calls + 1);       /* right subproblem */
+    calls = EXEN(st, SI, s - 2, calls + 1);       /* left subproblem */
+    return calls;
+}
+
+/* MAGNET for a pattern P of length mp <= m against a text T of length m,
+ * with the count modes of oracle_count_mode.  Writes the MAGNET vector to V
+ * (m bytes) when not NULL; returns the count, or -1. */
+int oracle_magnet_mode(const char *P, int mp, const char *T, int m, int E, int mode,
+                       uint8_t *V)
+{
+    if (m <= 0 || mp < 0 || mp > m || E < 0 || mode < 0 || mode > 3)
+        return -1;
+    uint8_t *map = (uint8_t *)malloc((size_t)(2 * E + 1) * m);
+    uint8_t *vec = (uint8_t *)malloc((size_t)m);
+    if (!map || !vec) {
+        free(map);
+        free(vec);
+        return -1;
+    }
+    build_map(P, mp, T, m, E, map);
+    for (int c = 0; c < m; ++c)
+        vec[c] = 1;
+    magnet_state st = {map, m, E, vec, 0};
+    EXEN(&st, 0, m - 1, 1);
+    if (st.rejected)
+        for (int c = 0; c < m; ++c)
+            vec[c] = 1;
+    int count = oracle_count_mode(vec, m, mode);
+    if (V)
+        memcpy(V, vec, (size_t)m);
+    free(map);
+    free(vec);
+    return count;
+}
