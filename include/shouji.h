@@ -164,7 +164,8 @@ shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
  * of the read in the paper's map.
  *
  *   vectors      device, bit-sliced Shouji bit-vectors of n_pairs pairs of
- *                length m (out_vectors of shouji_filter).
+ *                length m (out_vectors of shouji_filter, or the MAGNET
+ *                bit-vectors of shouji_magnet).
  *   E, E_per_pair as shouji_filter (the accept threshold).
  *   mode         one of the four modes above.
  *   out_accept   device uint32[ceil(n_pairs / 32)]: count <= E.
@@ -181,6 +182,35 @@ shouji_status shouji_count(const uint32_t *vectors, uint32_t m, size_t n_pairs,
                            int E, const uint8_t *E_per_pair, int mode,
                            uint32_t *out_accept, uint8_t *out_count,
                            void *stream);
+
+/*
+ * shouji_magnet -- the MAGNET filter (Supplementary Sec. 7, Algorithms 3
+ * and 4 of the paper) on the same packed pairs and the same neighborhood
+ * map as shouji_filter.
+ *
+ * Per pair: the MAGNET bit-vector starts as all ones.  An extraction takes,
+ * inside the current column range, the longest run of zeros over the 2E+1
+ * diagonals, writes it as zeros into the vector, and keeps the column just
+ * before and just after it out of both subranges (encapsulation); the
+ * subrange right of the run is solved first, with all of its own
+ * subranges, then the subrange left of it.  There are at most E+1
+ * extractions, and a range without a zero extracts nothing.  If the first
+ * run is shorter than ceil((m-E)/(E+1)) columns the pair is rejected with
+ * the vector left all ones.  Ties between equally long runs go to upper_1,
+ * lower_1, upper_2, lower_2, ... in that order, to the main diagonal only
+ * when no other diagonal has a run that long, and within a diagonal to the
+ * leftmost run.  The pair is accepted iff the vector holds at most E ones.
+ *
+ * Arguments, layouts and errors are those of shouji_filter; out_vectors
+ * receives the MAGNET bit-vectors in the bit-sliced layout of an N mask,
+ * which shouji_count recounts for local and glocal alignment.
+ */
+shouji_status shouji_magnet(const uint32_t *reads, const uint32_t *refs,
+                            const uint32_t *reads_nmask,
+                            const uint32_t *refs_nmask, uint32_t m,
+                            size_t n_pairs, int E, const uint8_t *E_per_pair,
+                            uint32_t *out_accept, uint8_t *out_count,
+                            uint32_t *out_vectors, void *stream);
 
 /*
  * shouji_compact_workspace_size -- bytes of device workspace that

@@ -26,7 +26,7 @@ __all__ = [
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
     "Batch", "Server", "shouji_count", "COUNT_GLOBAL", "COUNT_LOCAL", "COUNT_GLOCAL_START",
-    "COUNT_GLOCAL_END",
+    "COUNT_GLOCAL_END", "shouji_magnet",
 ]
 
 COUNT_GLOBAL, COUNT_LOCAL, COUNT_GLOCAL_START, COUNT_GLOCAL_END = 0, 1, 2, 3
@@ -64,6 +64,8 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_pack.restype = ctypes.c_int
     lib.shouji_filter.argtypes = [vp, vp, vp, vp, u32, sz, ctypes.c_int, vp, vp, vp, vp, vp]
     lib.shouji_filter.restype = ctypes.c_int
+    lib.shouji_magnet.argtypes = [vp, vp, vp, vp, u32, sz, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.shouji_magnet.restype = ctypes.c_int
     lib.shouji_compact_workspace_size.argtypes = [sz]
     lib.shouji_compact_workspace_size.restype = sz
     lib.shouji_compact.argtypes = [vp, sz, vp, vp, vp, sz, vp]
@@ -196,6 +198,29 @@ def shouji_filter(reads, refs, m: int, n_pairs: int, E: int, *, reads_nmask=None
                              m, n_pairs, E, _ptr(E_per_pair), _ptr(out_accept),
                              _ptr(out_count), _ptr(out_vectors), _stream(stream)),
            "shouji_filter")
+    return out_accept, out_count, out_vectors
+
+
+def shouji_magnet(reads, refs, m: int, n_pairs: int, E: int, *, reads_nmask=None,
+                  refs_nmask=None, E_per_pair=None, out_accept=None, out_count=None,
+                  count: bool = True, out_vectors=None, vectors: bool = False,
+                  stream=None):
+    """MAGNET on packed pairs, same arguments and results as ``shouji_filter``
+    (``vectors`` are the MAGNET bit-vectors)."""
+    torch = _torch()
+    lib = load_library()
+    dev = reads.device
+    if out_accept is None:
+        out_accept = torch.empty(max(1, (n_pairs + 31) // 32), dtype=torch.int32, device=dev)
+    if out_count is None and count:
+        out_count = torch.empty(max(1, n_pairs), dtype=torch.uint8, device=dev)
+    if out_vectors is None and vectors:
+        out_vectors = torch.empty(max(1, lib.shouji_nmask_words(n_pairs, m)), dtype=torch.int32,
+                                  device=dev)
+    _check(lib.shouji_magnet(_ptr(reads), _ptr(refs), _ptr(reads_nmask), _ptr(refs_nmask),
+                             m, n_pairs, E, _ptr(E_per_pair), _ptr(out_accept),
+                             _ptr(out_count), _ptr(out_vectors), _stream(stream)),
+           "shouji_magnet")
     return out_accept, out_count, out_vectors
 
 

@@ -19,7 +19,7 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for fn in ("shouji_pack", "shouji_filter", "shouji_compact",
+    for fn in ("shouji_pack", "shouji_filter", "shouji_magnet", "shouji_compact",
                "shouji_compact_workspace_size", "shouji_status_string"):
         assert fn in names
 
@@ -67,6 +67,16 @@ def test_host_argument_checks_return_einval():
     assert lib.shouji_filter(ctypes.c_void_p(0x1004), fake, None, None, 100, 10, 5, None, fake,
                              None, None, None) == EINVAL
     assert lib.shouji_filter(None, None, None, None, 100, 0, 5, None, None, None, None, None) == OK
+    # magnet: the checks of the filter
+    assert lib.shouji_magnet(fake, fake, None, None, 100, 10, -1, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_magnet(fake, fake, None, None, 100, 10, 32, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_magnet(fake, fake, None, None, 256, 10, 5, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_magnet(fake, fake, None, fake, 100, 10, 5, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_magnet(fake, None, None, None, 100, 10, 5, None, fake, None, None, None) == EINVAL
+    assert lib.shouji_magnet(fake, fake, None, None, 100, 10, 5, None, None, None, None, None) == EINVAL
+    assert lib.shouji_magnet(fake, ctypes.c_void_p(0x1004), None, None, 100, 10, 5, None, fake,
+                             None, None, None) == EINVAL
+    assert lib.shouji_magnet(None, None, None, None, 100, 0, 5, None, None, None, None, None) == OK
     # compact: short or misaligned workspace, too many pairs, nulls
     assert lib.shouji_compact(fake, 1000, fake, fake, fake, 0, None) == EINVAL
     assert lib.shouji_compact(fake, 1000, fake, fake, ctypes.c_void_p(0x1008), 1 << 20, None) == EINVAL

@@ -1,0 +1,133 @@
+"""shouji_magnet (MAGNET, Supplementary Sec. 7, Algorithms 3-4) against the
+oracle, pair by pair: counts, accept bits and the MAGNET bit-vectors."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1809_07858_gb300 as sj
+from paper_1809_07858_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _bits(acc, n):
+    w = acc.cpu().numpy().view(np.uint32)
+    return ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1)[:n].astype(bool)
+
+
+def _vector(vec, m, i):
+    """Column bits of pair i from the bit-sliced vector words."""
+    t, l, b = i // 1024, (i % 1024) // 32, i % 32
+    cols = vec[(t * m + np.arange(m)) * 32 + l]
+    return ((cols >> np.uint32(b)) & 1).astype(np.uint8)
+
+
+def _run(reads, refs, m, E, *, with_n, E_per_pair=None):
+    dev = _dev()
+    n = reads.shape[0]
+    pr, nr = sj.shouji_pack(torch.from_numpy(np.ascontiguousarray(reads)).to(dev), m, with_n=with_n)
+    pt, nt = sj.shouji_pack(torch.from_numpy(np.ascontiguousarray(refs)).to(dev), m, with_n=with_n)
+    ep = None if E_per_pair is None else torch.from_numpy(E_per_pair).to(dev)
+    acc, cnt, vec = sj.shouji_magnet(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
+                                     E_per_pair=ep, vectors=True)
+    torch.cuda.synchronize()
+    return (_bits(acc, n), cnt[:n].cpu().numpy(),
+            vec.cpu().numpy().view(np.uint32), acc.cpu().numpy().view(np.uint32))
+
+
+def _check(reads, refs, m, E, bits, cnt, vec, E_per_pair=None, idx=None):
+    idx = range(reads.shape[0]) if idx is None else idx
+    for i in idx:
+        e = E if E_per_pair is None else min(int(E_per_pair[i]), E)
+        V, c = oracle.magnet(reads[i].tobytes(), refs[i].tobytes(), e)
+        assert cnt[i] == c, (i, cnt[i], c)
+        assert bits[i] == (c <= e), i
+        assert (_vector(vec, m, i) == V).all(), i
+
+
+@pytest.mark.parametrize("m,E,with_n", [(100, 5, False), (100, 5, True), (100, 2, False),
+                                        (150, 7, False), (250, 12, True), (33, 3, False),
+                                        (64, 0, False), (96, 9, False), (255, 31, False)])
+def test_magnet_bit_exact(m, E, with_n):
+    n = 2500  # three tiles, the last one ragged
+    reads, refs = synth.pairs(n, m, seed=7 * m + E, near=(0, E + 1), far=(E + 1, m // 3 + 2),
+                              far_fraction=0.5, n_rate=0.01 if with_n else 0.0)
+    bits, cnt, vec, words = _run(reads, refs, m, E, with_n=with_n)
+    _check(reads, refs, m, E, bits, cnt, vec)
+    assert (words[-1] >> np.uint32(n % 32)) == 0 if n % 32 else True
+
+
+def test_magnet_per_pair_threshold():
+    m, E, n = 100, 10, 3000
+    reads, refs = synth.pairs(n, m, seed=91, near=(0, 10), far=(11, 30), far_fraction=0.4)
+    ep = np.random.default_rng(5).integers(0, E + 4, size=n).astype(np.uint8)  # some above E
+    bits, cnt, vec, _ = _run(reads, refs, m, E, with_n=False, E_per_pair=ep)
+    _check(reads, refs, m, E, bits, cnt, vec, E_per_pair=ep)
+
+
+def test_magnet_edge_cases():
+    rng = np.random.default_rng(11)
+    for m in (1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 224, 255):
+        for E in (0, 1, 4, 31):
+            n = 70
+            reads = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=(n, m))
+            refs = reads.copy()
+            refs[10:40] = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=(30, m))  # random
+            refs[40:50] = rng.choice(np.frombuffer(b"GT", np.uint8), size=(10, m))
+            reads[40:50] = rng.choice(np.frombuffer(b"AC", np.uint8), size=(10, m))  # disjoint
+            refs[50:70, :] = np.roll(reads[50:70], 1 + (m // 7), axis=1)  # shifted copies
+            bits, cnt, vec, _ = _run(reads, refs, m, E, with_n=False)
+            _check(reads, refs, m, E, bits, cnt, vec)
+
+
+def test_magnet_count_modes_with_short_reads():
+    """MAGNET vectors recounted by shouji_count (local / glocal), with reads
+    shorter than their reference packed as 'N' padding."""
+    dev = _dev()
+    m, E, n = 100, 4, 2000
+    rng = np.random.default_rng(3)
+    reads, refs = synth.pairs(n, m, seed=33, near=(0, E), far=(E + 1, 30), far_fraction=0.5)
+    short = rng.random(n) < 0.4
+    mp = np.where(short, rng.integers(m // 2, m + 1, size=n), m)
+    for i in np.flatnonzero(short):
+        reads[i, mp[i]:] = ord("N")
+    bits, cnt, vec, _ = _run(reads, refs, m, E, with_n=True)
+    vec_t = torch.from_numpy(vec.view(np.int32)).to(dev)
+    for mode in range(4):
+        acc, c = sj.shouji_count(vec_t, m, n, E, mode)
+        torch.cuda.synchronize()
+        c = c[:n].cpu().numpy()
+        b = _bits(acc, n)
+        for i in range(n):
+            _, co = oracle.magnet(reads[i, :mp[i]].tobytes(), refs[i].tobytes(), E, mode)
+            assert c[i] == co, (mode, i)
+            assert b[i] == (co <= E)
+
+
+def test_magnet_full_size_sampled():
+    """The benchmark's MAGNET workload (30M pairs, m = 100, E = 5, half of them
+    near, half far) in one launch, checked on a sample of pairs."""
+    dev = _dev()
+    n, m, E = 30_000_000, 100, 5
+    reads, refs = synth.workload("sweep", n, E=E)
+    pr, _ = sj.shouji_pack(torch.from_numpy(reads).to(dev), m)
+    pt, _ = sj.shouji_pack(torch.from_numpy(refs).to(dev), m)
+    acc, cnt, _ = sj.shouji_magnet(pr, pt, m, n, E)
+    torch.cuda.synchronize()
+    bits = _bits(acc, n)
+    cnt = cnt.cpu().numpy()
+    idx = np.random.default_rng(0).choice(n, 3000, replace=False)
+    idx = np.concatenate([idx, np.arange(n - 40, n)])
+    for i in idx:
+        _, c = oracle.magnet(reads[i].tobytes(), refs[i].tobytes(), E)
+        assert cnt[i] == c, i
+        assert bits[i] == (c <= E), i
+    del pr, pt, acc, cnt
+    torch.cuda.empty_cache()
