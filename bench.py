@@ -150,10 +150,10 @@ def workload_config(n):
             "l2": "inputs larger than L2 (%.1f GB ASCII per step); no flush" % (2 * n * M / 1e9)}
 
 
-def cpu_oracle_rate(reads, refs, threads):
+def cpu_oracle_rate(reads, refs, threads, magnet=False):
     import oracle
     t0 = time.perf_counter()
-    oracle.shouji_batch(reads, refs, E, threads=threads)
+    oracle.shouji_batch(reads, refs, E, threads=threads, magnet=magnet)
     return len(reads) / (time.perf_counter() - t0)
 
 
@@ -234,6 +234,40 @@ def run_batched(args, dev, peak_ops):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                          "unit": "lane-ops/s", "frac": achieved / peak_ops,
                          "scope": "whole batch step (bucketing, packing, filters, gather)"}}
+
+
+def run_magnet(args, dev, packed_r, packed_t, n, shouji_accept):
+    """MAGNET (Supplementary Sec. 7) on the same packed batch as the headline
+    step: shouji_magnet alone, inputs packed and resident in HBM."""
+    import numpy as np
+    import torch
+
+    import paper_1809_07858_gb300 as sj
+    acc = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        sj.shouji_magnet(packed_r, packed_t, M, n, E, out_accept=acc, out_count=cnt, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.magnet_steps):
+        sj.shouji_magnet(packed_r, packed_t, M, n, E, out_accept=acc, out_count=cnt, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.magnet_steps
+    m_words = acc.cpu().numpy().view(np.uint32)
+    s_words = shouji_accept.cpu().numpy().view(np.uint32)
+
+    def ones(w):
+        return int(np.unpackbits(w.view(np.uint8)).sum())
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.magnet_steps,
+            "kernel": "shouji_magnet", "workload": "the headline's %d pairs (m=%d, E=%d), "
+            "packed and resident" % (n, M, E),
+            "accepted": ones(m_words), "accepted_shouji": ones(s_words),
+            "accepted_magnet_not_shouji": ones(m_words & ~s_words),
+            "accepted_shouji_not_magnet": ones(s_words & ~m_words)}
 
 
 def run_served(args, dev):
@@ -431,7 +465,9 @@ def run_ours(args, world, rank, local):
     e2e_value = world * n * args.e2e_steps / e2e_s
     h2d = 2 * n * M
     d2h = h_acc.numel() * 4 + n + 4 * n_accepted
-    batched = served = None
+    batched = served = magnet = None
+    if world == 1 and args.magnet_steps > 0:
+        magnet = run_magnet(args, dev, packed_r, packed_t, n, accept)
     if world == 1:
         del d_reads, d_refs, packed_r, packed_t, idx
         torch.cuda.empty_cache()
@@ -446,6 +482,13 @@ def run_ours(args, world, rank, local):
         rate = cpu_oracle_rate(h_reads[:sample].numpy(), h_refs[:sample].numpy(), threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "pairs 0..%d of the same workload (%d threads)" % (sample - 1, threads)}
+        if magnet is not None:
+            msample = max(1, sample // 10)
+            mrate = cpu_oracle_rate(h_reads[:msample].numpy(), h_refs[:msample].numpy(), threads,
+                                    magnet=True)
+            magnet["cpu_baseline"] = {"value": mrate, "unit": UNIT, "cores": threads,
+                                      "kind": "oracle", "sample": "pairs 0..%d (%d threads)" % (
+                                          msample - 1, threads)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -467,6 +510,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "batched": batched,
         "served": served,
+        "magnet": magnet,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -492,6 +536,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--magnet-steps", type=int, default=5, help="0 skips the MAGNET leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

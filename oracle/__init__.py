@@ -70,6 +70,8 @@ def _load():
                                             ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_int]
         lib.oracle_shouji_batch.restype = ctypes.c_int
+        lib.oracle_magnet_batch.argtypes = lib.oracle_shouji_batch.argtypes
+        lib.oracle_magnet_batch.restype = ctypes.c_int
         lib.oracle_count_mode.argtypes = [u8p, ctypes.c_int, ctypes.c_int]
         lib.oracle_count_mode.restype = ctypes.c_int
         lib.oracle_shouji_mode.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p,
@@ -164,8 +166,9 @@ def edit_distance(a, b) -> int:
 
 
 def shouji_batch(reads: np.ndarray, refs: np.ndarray, E: int,
-                 E_per_pair: np.ndarray | None = None, threads: int = 1):
-    """Filter n pairs given as (n, m) uint8 arrays (row i = pair i).
+                 E_per_pair: np.ndarray | None = None, threads: int = 1, magnet: bool = False):
+    """Filter n pairs given as (n, m) uint8 arrays (row i = pair i) with Shouji,
+    or with MAGNET (global count) when ``magnet``.
 
     Returns (accept bool[n], count uint8[n]).  ``threads`` splits the pairs
     into contiguous ranges, one POSIX thread each.
@@ -181,9 +184,9 @@ def shouji_batch(reads: np.ndarray, refs: np.ndarray, E: int,
         E_per_pair = np.ascontiguousarray(E_per_pair, dtype=np.uint8)
         assert E_per_pair.shape == (n,)
         ep = E_per_pair.ctypes.data
-    rc = _load().oracle_shouji_batch(reads.ctypes.data, refs.ctypes.data, m, m,
-                                     n, E, ep, accept.ctypes.data,
-                                     count.ctypes.data, int(threads))
+    fn = _load().oracle_magnet_batch if magnet else _load().oracle_shouji_batch
+    rc = fn(reads.ctypes.data, refs.ctypes.data, m, m, n, E, ep, accept.ctypes.data,
+            count.ctypes.data, int(threads))
     if rc != 0:
         raise MemoryError("oracle_shouji_batch failed")
     return accept.astype(bool), count

@@ -278,15 +278,20 @@ typedef struct {
     uint8_t *accept, *count;
     size_t lo, hi;
     int failed;
+    int magnet;  /* 0: Shouji, 1: MAGNET (global count) */
 } batch_job;
+
+int oracle_magnet_mode(const char *P, int mp, const char *T, int m, int E, int mode,
+                       uint8_t *V);
 
 static void *batch_worker(void *arg)
 {
     batch_job *job = (batch_job *)arg;
     for (size_t i = job->lo; i < job->hi; ++i) {
         int E = job->E_per_pair ? job->E_per_pair[i] : job->E;
-        int ones = oracle_shouji(job->reads + i * job->stride,
-                                 job->refs + i * job->stride, job->m, E, NULL);
+        const char *P = job->reads + i * job->stride, *T = job->refs + i * job->stride;
+        int ones = job->magnet ? oracle_magnet_mode(P, job->m, T, job->m, E, 0, NULL)
+                               : oracle_shouji(P, T, job->m, E, NULL);
         if (ones < 0) {
             job->failed = 1;
             return NULL;
@@ -299,9 +304,9 @@ static void *batch_worker(void *arg)
     return NULL;
 }
 
-int oracle_shouji_batch(const char *reads, const char *refs, size_t stride,
-                        int m, size_t n, int E, const uint8_t *E_per_pair,
-                        uint8_t *accept, uint8_t *count, int threads)
+static int run_batch(const char *reads, const char *refs, size_t stride, int m, size_t n,
+                     int E, const uint8_t *E_per_pair, uint8_t *accept, uint8_t *count,
+                     int threads, int magnet)
 {
     if (threads < 1)
         threads = 1;
@@ -318,7 +323,7 @@ int oracle_shouji_batch(const char *reads, const char *refs, size_t stride,
     for (int t = 0; t < threads; ++t) {
         size_t len = per + ((size_t)t < extra ? 1 : 0);
         jobs[t] = (batch_job){reads, refs, stride, m, E, E_per_pair,
-                              accept, count, at, at + len, 0};
+                              accept, count, at, at + len, 0, magnet};
         at += len;
     }
     int failed = 0;
@@ -337,6 +342,21 @@ int oracle_shouji_batch(const char *reads, const char *refs, size_t stride,
     free(jobs);
     free(tids);
     return failed ? -1 : 0;
+}
+
+int oracle_shouji_batch(const char *reads, const char *refs, size_t stride,
+                        int m, size_t n, int E, const uint8_t *E_per_pair,
+                        uint8_t *accept, uint8_t *count, int threads)
+{
+    return run_batch(reads, refs, stride, m, n, E, E_per_pair, accept, count, threads, 0);
+}
+
+/* MAGNET over a batch of equal-length pairs (global count), as above. */
+int oracle_magnet_batch(const char *reads, const char *refs, size_t stride,
+                        int m, size_t n, int E, const uint8_t *E_per_pair,
+                        uint8_t *accept, uint8_t *count, int threads)
+{
+    return run_batch(reads, refs, stride, m, n, E, E_per_pair, accept, count, threads, 1);
 }
 
 /* ====================================================================== */

@@ -20,12 +20,19 @@
 //  - diagonal d's matches are "P moved by d columns equals T" on both
 //    bit-planes, with columns out of the band, N columns and columns outside
 //    the range cleared: six logic ops per word;
-//  - the longest run of ones of a mask comes from the ladder A_1 = x,
-//    A_2L = A_L & (A_L >> L), which stops at its first empty level and so
-//    bounds the run to [2^(k-1), 2^k); a diagonal whose bound cannot beat the
-//    best run so far is dropped there, otherwise the descent
-//    A_(L+h) = A_h & (A_L >> h) over the stored levels gives the exact
-//    length, and the lowest set bit of A_L the leftmost start;
+//  - runs are measured with the ladder A_1 = x, A_2L = A_L & (A_L >> L): the
+//    first empty level bounds the longest run to [2^(k-1), 2^k), the descent
+//    A_(L+h) = A_h & (A_L >> h) gives its exact length, and the lowest set
+//    bit of A_L its leftmost start;
+//  - lanes of a warp run different pairs, so the work is arranged to keep
+//    them on the same instructions.  Every diagonal gets the same cheap test
+//    (A_1 ... A_8), which settles runs shorter than 8 columns.  The few
+//    diagonals with a longer run (about one to three per similar pair) are
+//    walked by each lane from its own list: the first extraction records all
+//    of their runs of 8 or more columns (the runs of A_8), and a later
+//    extraction only clips that list to its range, running the cheap test
+//    again only when no listed run of 8 reaches into the range.  A pair with
+//    more long runs than the list holds uses the full ladder instead;
 //  - the recursion is an explicit stack of column ranges: the left range is
 //    pushed under the right one, so the right range and all of its own
 //    subranges are solved first, as in Algorithm 4.
@@ -39,6 +46,9 @@ namespace {
 
 constexpr int kMagnetThreads = 128;
 constexpr int kMaxStack = SHOUJI_MAX_E + 3;  // 1 + one net push per extraction
+constexpr int kMainRank = 2 * SHOUJI_MAX_E;  // after every upper_j and lower_j
+constexpr int kLong = 8;                     // runs this long are listed
+constexpr int kMaxRuns = 32;                 // listed runs per pair
 
 __device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane)
 {
@@ -98,110 +108,121 @@ __device__ __forceinline__ uint32_t down_word(const uint32_t *x, int h, int w)
     return __funnelshift_r(x[w], w + 1 < W ? x[w + 1] : 0u, h);
 }
 
-// Exact run length from the ladder whose top non-empty level is K-1:
-// A_(L+h) = A_h & (A_L >> h) for h = 2^(K-2) ... 1.
-template <int W, int LV, int K>
-__device__ __forceinline__ void descend(const uint32_t *lv, uint32_t (&cur)[W], int &L)
+// A run of length L on a diagonal of rank `rank` replaces the best run so far
+// iff it is longer, or as long and of a lower rank.
+__device__ __forceinline__ bool beats(int L, int rank, int best_len, int best_rank)
 {
-#pragma unroll
-    for (int w = 0; w < W; ++w)
-        cur[w] = lv[(K - 1) * W + w];
-    L = 1 << (K - 1);
-#pragma unroll
-    for (int j = K - 2; j >= 0; --j) {
-        uint32_t t[W], o = 0u;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            t[w] = lv[j * W + w] & down_word<W>(cur, 1 << j, w);
-            o |= t[w];
-        }
-        if (o) {
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                cur[w] = t[w];
-            L += 1 << j;
-        }
-    }
+    return L > best_len || (L == best_len && rank < best_rank);
 }
 
-// Longest run of ones in x and its leftmost start, if it beats `floor_len`
-// (or ties with it when tie_ok); otherwise 0.  The descent is dispatched on
-// the ladder height k so that every level is read at a constant index and
-// the ladder stays in registers.
+// The same with the leftmost-run rule inside one diagonal: of two equally
+// long runs of the same diagonal the one that starts first is kept.
+__device__ __forceinline__ bool beats_at(int L, int rank, int start, int best_len,
+                                         int best_rank, int best_s)
+{
+    return L > best_len ||
+           (L == best_len && (rank < best_rank || (rank == best_rank && start < best_s)));
+}
+
+// Longest run of ones in x and its leftmost start, or 0 when it cannot beat
+// the best run so far.  `k` receives the ladder height (the run lies in
+// [2^(k-1), 2^k), k = 0 for an empty x).  Every lane takes the same code
+// path whatever its ladder height: levels a lane does not need are skipped
+// by a predicate, not by a branch to other code.
 template <int W>
-__device__ __forceinline__ int longest_run(const uint32_t (&x)[W], int floor_len, bool tie_ok,
-                                           int &start)
+__device__ __forceinline__ int longest_run(const uint32_t (&x)[W], int rank, int best_len,
+                                           int best_rank, int &start, int &k)
 {
     constexpr int LV = ladder_levels<W>();
-    uint32_t lv[LV * W];
+    uint32_t lv[LV][W], top[W];
 #pragma unroll
     for (int w = 0; w < W; ++w)
-        lv[w] = x[w];
-    if (!any(x))
+        lv[0][w] = top[w] = x[w];
+    k = any(x) ? 1 : 0;
+    if (k == 0)
         return 0;
-    int k = 1;  // levels 0 .. k-1 are non-empty
 #pragma unroll
     for (int j = 1; j < LV; ++j) {
-        if (k == j) {
+        if (k == j) {  // A_(2^j) = A_(2^(j-1)) & (A_(2^(j-1)) >> 2^(j-1))
             uint32_t o = 0u;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                lv[j * W + w] = lv[(j - 1) * W + w] & down_word<W>(lv + (j - 1) * W, 1 << (j - 1), w);
-                o |= lv[j * W + w];
+                lv[j][w] = lv[j - 1][w] & down_word<W>(lv[j - 1], 1 << (j - 1), w);
+                o |= lv[j][w];
             }
-            if (o)
+            if (o) {
                 k = j + 1;
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    top[w] = lv[j][w];
+            }
         }
     }
-    const int bound = (1 << k) - 1;
-    if (bound < floor_len || (bound == floor_len && !tie_ok))
+    if (!beats((1 << k) - 1, rank, best_len, best_rank))
         return 0;
-    uint32_t cur[W];
-    int L = 0;
-    switch (k) {
-#define SHOUJI_DESCENT_CASE(K)                                   \
-    case K:                                                      \
-        if (K <= LV)                                             \
-            descend<W, LV, (K <= LV ? K : 1)>(lv, cur, L);       \
-        break;
-        SHOUJI_DESCENT_CASE(1)
-        SHOUJI_DESCENT_CASE(2)
-        SHOUJI_DESCENT_CASE(3)
-        SHOUJI_DESCENT_CASE(4)
-        SHOUJI_DESCENT_CASE(5)
-        SHOUJI_DESCENT_CASE(6)
-        SHOUJI_DESCENT_CASE(7)
-        SHOUJI_DESCENT_CASE(8)
-#undef SHOUJI_DESCENT_CASE
+    // Descent: A_(L+h) = A_h & (A_L >> h), h = 2^(k-2) ... 1.
+    int L = 1 << (k - 1);
+#pragma unroll
+    for (int j = LV - 2; j >= 0; --j) {
+        if (j < k - 1) {
+            uint32_t t[W], o = 0u;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                t[w] = lv[j][w] & down_word<W>(top, 1 << j, w);
+                o |= t[w];
+            }
+            if (o) {
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    top[w] = t[w];
+                L += 1 << j;
+            }
+        }
     }
-    if (L < floor_len || (L == floor_len && !tie_ok))
+    if (!beats(L, rank, best_len, best_rank))
         return 0;
     int s = 0;
 #pragma unroll
     for (int w = W - 1; w >= 0; --w)
-        if (cur[w])
-            s = 32 * w + __ffs(cur[w]) - 1;
+        if (top[w])
+            s = 32 * w + __ffs(top[w]) - 1;
     start = s;
     return L;
 }
 
+// One pair in flight: its sequences as column masks, its MAGNET vector and
+// its recursion state.  Br = read columns that match nothing (N, or past the
+// end of the read), Nt = reference N columns.
+template <int W>
+struct PairState {
+    uint32_t Rh[W], Rl[W], Th[W], Tl[W], Br[W], Nt[W], V[W];
+    uint64_t cand;  // diagonals with a run of at least kLong columns (bit = slot)
+    int nruns;      // runs in PairStack::runs; -1 once they did not fit
+    int Ep;         // the pair's threshold
+    int done;       // extractions so far
+    int sp;         // ranges on the stack
+    bool rejected;  // the first run was too short
+};
+
+// The dynamically indexed part of a pair's state, kept apart from PairState
+// so that the column masks stay in registers.  Diagonals are numbered by
+// slot: 0 = main, 2j-1 = upper_j, 2j = lower_j.
+struct PairStack {
+    uint16_t range[kMaxStack];          // column ranges [lo | hi << 8]
+    uint8_t len[2 * SHOUJI_MAX_E + 1];  // longest run of each diagonal over all columns
+    uint32_t runs[kMaxRuns];            // runs of kLong or more: start | end << 8 | slot << 16
+};
+
+// Column masks of pair `lane` of group g (32 pairs of one tile lane), read
+// 32 positions at a time and turned around by the warp transpose.  Every
+// lane of the warp must take part.
 template <int W, bool WITH_N>
-__global__ void __launch_bounds__(kMagnetThreads)
-magnet_kernel(const FilterArgs a, const int E)
+__device__ __forceinline__ void load_group(const FilterArgs &a, size_t g, int lane,
+                                           uint32_t (&P)[6][W])
 {
-    const int lane = threadIdx.x & 31;
-    const size_t g = (size_t)blockIdx.x * (kMagnetThreads / 32) + (threadIdx.x >> 5);
-    if (g >= groups_of(a.n_pairs))
-        return;  // whole warp
     const int m = a.m;
     const size_t t = g / kLanes;
     const int l = (int)(g % kLanes);
-    const size_t pair = g * 32 + lane;
-    const bool live = pair < a.n_pairs;
-
-    // The pair's sequences as column masks; Br = read columns that match
-    // nothing (N, or past the end), Nt = reference N columns.
-    uint32_t Rh[W], Rl[W], Th[W], Tl[W], Br[W], Nt[W], Mv[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         const int p = 32 * w + lane;
@@ -216,112 +237,419 @@ magnet_kernel(const FilterArgs a, const int E)
                 nf = __ldg(a.refs_n + idx);
             }
         }
-        Rh[w] = warp_transpose(r.x, lane);
-        Rl[w] = warp_transpose(r.y, lane);
-        Th[w] = warp_transpose(f.x, lane);
-        Tl[w] = warp_transpose(f.y, lane);
-        Mv[w] = span_mask(0, m - 1, w);
-        Br[w] = ~Mv[w];
-        Nt[w] = 0u;
-        if (WITH_N) {
-            Br[w] |= warp_transpose(nr, lane);
-            Nt[w] = warp_transpose(nf, lane);
-        }
+        P[0][w] = warp_transpose(r.x, lane);
+        P[1][w] = warp_transpose(r.y, lane);
+        P[2][w] = warp_transpose(f.x, lane);
+        P[3][w] = warp_transpose(f.y, lane);
+        P[4][w] = WITH_N ? warp_transpose(nr, lane) : 0u;
+        P[5][w] = WITH_N ? warp_transpose(nf, lane) : 0u;
     }
+}
 
-    int Ep = E;
-    if (a.E_per_pair && live)
-        Ep = min((int)__ldg(a.E_per_pair + pair), E);
+template <int W>
+__device__ __forceinline__ void init_pair(PairState<W> &st, PairStack &sk,
+                                          const uint32_t (&P)[6][W], int m, int Ep)
+{
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const uint32_t mv = span_mask(0, m - 1, w);
+        st.Rh[w] = P[0][w];
+        st.Rl[w] = P[1][w];
+        st.Th[w] = P[2][w];
+        st.Tl[w] = P[3][w];
+        st.Br[w] = P[4][w] | ~mv;
+        st.Nt[w] = P[5][w];
+        st.V[w] = mv;
+    }
+    st.cand = 0ull;
+    st.nruns = 0;
+    st.Ep = Ep;
+    st.done = 0;
+    st.rejected = false;
+    sk.range[0] = (uint16_t)((m - 1) << 8);  // range [0, m-1]
+    st.sp = 1;
+}
 
-    uint32_t V[W];
+// Rank of a slot in the order of preference between equally long runs:
+// upper_j has rank 2(j-1), lower_j rank 2(j-1)+1, the main diagonal last.
+__device__ __forceinline__ int rank_of(int slot) { return slot ? slot - 1 : kMainRank; }
+
+// Matches of the diagonal in `slot` inside the columns of G.  The direction
+// is a run-time value: the read is moved by a funnel shift whose operand
+// pair and amount are chosen per lane (upper_j: up by j; lower_j: down by j;
+// main: not moved).
+template <int W>
+__device__ __forceinline__ void build_any(const PairState<W> &st, const uint32_t (&G)[W],
+                                          int slot, uint32_t (&x)[W])
+{
+    const int j = (slot + 1) >> 1;
+    const bool up = (slot & 1) != 0;
+    const int n = up ? 32 - j : j;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int pv = w ? w - 1 : 0, nx = w + 1 < W ? w + 1 : 0;
+        const uint32_t hl = up ? (w ? st.Rh[pv] : 0u) : st.Rh[w];
+        const uint32_t hh = up ? st.Rh[w] : (w + 1 < W ? st.Rh[nx] : 0u);
+        const uint32_t ll = up ? (w ? st.Rl[pv] : 0u) : st.Rl[w];
+        const uint32_t lh = up ? st.Rl[w] : (w + 1 < W ? st.Rl[nx] : 0u);
+        const uint32_t bl = up ? (w ? st.Br[pv] : 0xFFFFFFFFu) : st.Br[w];
+        const uint32_t bh = up ? st.Br[w] : (w + 1 < W ? st.Br[nx] : 0xFFFFFFFFu);
+        const uint32_t h = __funnelshift_rc(hl, hh, n);
+        const uint32_t lo = __funnelshift_rc(ll, lh, n);
+        const uint32_t b = __funnelshift_rc(bl, bh, n);
+        x[w] = ~((h ^ st.Th[w]) | (lo ^ st.Tl[w]) | b) & G[w];
+    }
+}
+
+// The same with the direction fixed at compile time (0: main, 1: upper_j,
+// -1: lower_j), for loops in which every lane examines the same diagonal.
+template <int W, int DIR>
+__device__ __forceinline__ void build_fixed(const PairState<W> &st, const uint32_t (&G)[W],
+                                            int j, uint32_t (&x)[W])
+{
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint32_t h, lo, b;
+        if (DIR > 0) {         // column c compares P[c - j] with T[c]
+            const int pv = w ? w - 1 : 0;
+            h = __funnelshift_l(w ? st.Rh[pv] : 0u, st.Rh[w], j);
+            lo = __funnelshift_l(w ? st.Rl[pv] : 0u, st.Rl[w], j);
+            b = __funnelshift_l(w ? st.Br[pv] : 0xFFFFFFFFu, st.Br[w], j);
+        } else if (DIR < 0) {  // column c compares P[c + j] with T[c]
+            const int nx = w + 1 < W ? w + 1 : 0;
+            h = __funnelshift_r(st.Rh[w], w + 1 < W ? st.Rh[nx] : 0u, j);
+            lo = __funnelshift_r(st.Rl[w], w + 1 < W ? st.Rl[nx] : 0u, j);
+            b = __funnelshift_r(st.Br[w], w + 1 < W ? st.Br[nx] : 0xFFFFFFFFu, j);
+        } else {
+            h = st.Rh[w];
+            lo = st.Rl[w];
+            b = st.Br[w];
+        }
+        x[w] = ~((h ^ st.Th[w]) | (lo ^ st.Tl[w]) | b) & G[w];
+    }
+}
+
+// Longest run of ones in x if it is shorter than kLong columns: its exact
+// length and leftmost start from the first levels of the ladder only
+// (A_1, A_2, A_4, A_8).  Returns -1 when x has a run of kLong or more.
+template <int W>
+__device__ __forceinline__ int short_run(const uint32_t (&x)[W], int &start)
+{
+    uint32_t a1[W], a2[W], a4[W], a8[W];
+    uint32_t o1 = 0u, o2 = 0u, o4 = 0u, o8 = 0u;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        a1[w] = x[w];
+        o1 |= a1[w];
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        a2[w] = a1[w] & down_word<W>(a1, 1, w);
+        o2 |= a2[w];
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        a4[w] = a2[w] & down_word<W>(a2, 2, w);
+        o4 |= a4[w];
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        a8[w] = a4[w] & down_word<W>(a4, 4, w);
+        o8 |= a8[w];
+    }
+    if (o8)
+        return -1;
+    if (!o1)
+        return 0;
+    // top non-empty level and its length
+    uint32_t cur[W];
+    int L;
 #pragma unroll
     for (int w = 0; w < W; ++w)
-        V[w] = live ? Mv[w] : 0u;
+        cur[w] = o4 ? a4[w] : o2 ? a2[w] : a1[w];
+    L = o4 ? 4 : o2 ? 2 : 1;
+    // descent: + 2 (only from A_4), + 1 (from A_4 or A_2)
+    if (o4) {
+        uint32_t t[W], o = 0u;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            t[w] = a2[w] & down_word<W>(cur, 2, w);
+            o |= t[w];
+        }
+        if (o) {
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                cur[w] = t[w];
+            L += 2;
+        }
+    }
+    if (o2) {
+        uint32_t t[W], o = 0u;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            t[w] = a1[w] & down_word<W>(cur, 1, w);
+            o |= t[w];
+        }
+        if (o) {
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                cur[w] = t[w];
+            L += 1;
+        }
+    }
+    int s = 0;
+#pragma unroll
+    for (int w = W - 1; w >= 0; --w)
+        if (cur[w])
+            s = 32 * w + __ffs(cur[w]) - 1;
+    start = s;
+    return L;
+}
 
-    uint16_t stack[kMaxStack];
-    int sp = 0;
-    if (live)
-        stack[sp++] = (uint16_t)((m - 1) << 8);  // range [0, m-1]
-    int done = 0;                                // extractions so far
-    const int first_min = m / (Ep + 1);          // ceil((m - E) / (E + 1))
+// The test of one diagonal for a run of kLong columns, in the first
+// extraction and in every later one alike (one code path for all lanes,
+// whatever step their pair is at).  A shorter run is settled here; a long
+// one, which only the first extraction can meet, marks the diagonal as a
+// candidate for the run list.  In later extractions this pass runs only when
+// the listed runs leave the best run shorter than kLong: a diagonal is
+// skipped when its bound (its longest short run over all columns, kLong - 1
+// for a candidate, and never more than the range) cannot beat the best so
+// far.  Candidates of a pair whose runs did not fit the list are left to the
+// ladder.
+template <int W, int DIR>
+__device__ __forceinline__ void short_pass(PairState<W> &st, PairStack &sk,
+                                           const uint32_t (&G)[W], int j, bool first,
+                                           int range_len, int &best_len, int &best_s,
+                                           int &best_rank)
+{
+    const int slot = DIR > 0 ? 2 * j - 1 : DIR < 0 ? 2 * j : 0;
+    const int rank = rank_of(slot);
+    const bool cand = ((st.cand >> slot) & 1ull) != 0;
+    if (cand && (first || st.nruns < 0))
+        return;
+    if (!first) {
+        const int ub = min(cand ? kLong - 1 : (int)sk.len[slot], range_len);
+        if (ub < best_len || (ub == best_len && rank > best_rank))
+            return;
+    }
+    uint32_t x[W];
+    build_fixed<W, DIR>(st, G, j, x);
+    int s = 0;
+    const int L = short_run(x, s);
+    if (L < 0) {
+        if (first)
+            st.cand |= 1ull << slot;
+        return;
+    }
+    if (first)
+        sk.len[slot] = (uint8_t)L;
+    if (L > 0 && beats_at(L, rank, s, best_len, best_rank, best_s)) {
+        best_len = L;
+        best_s = s;
+        best_rank = rank;
+    }
+}
 
-    while (sp > 0 && done <= Ep) {
-        const uint32_t range = stack[--sp];
-        const int SI = (int)(range & 0xFFu), EI = (int)(range >> 8);
-        uint32_t G[W];
+// Lowest set bit of a column mask (32 W when empty).
+template <int W>
+__device__ __forceinline__ int lowest(const uint32_t (&y)[W])
+{
+    int p = 32 * W;
+#pragma unroll
+    for (int w = W - 1; w >= 0; --w)
+        if (y[w])
+            p = 32 * w + __ffs(y[w]) - 1;
+    return p;
+}
+
+// First extraction, one candidate diagonal: its runs of kLong columns or more
+// are the runs of A_8 = x & (x >> 1) & ... & (x >> 7), each lengthened by
+// kLong - 1 columns.  They are walked from the left, appended to the run list
+// and offered as the best run.  Returns the longest.  When the list is full
+// the pair turns to the ladder for every candidate (nruns = -1).
+template <int W>
+__device__ __forceinline__ int list_runs(PairState<W> &st, PairStack &sk,
+                                         const uint32_t (&x)[W], int slot, int &best_len,
+                                         int &best_s, int &best_rank)
+{
+    uint32_t y[W], t[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        t[w] = x[w] & down_word<W>(x, 1, w);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        y[w] = t[w] & down_word<W>(t, 2, w);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        t[w] = y[w] & down_word<W>(y, 4, w);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        y[w] = t[w];
+    const int rank = rank_of(slot);
+    int longest = 0;
+    while (any(y)) {
+        const int a = lowest(y);
+        uint32_t z[W];
 #pragma unroll
         for (int w = 0; w < W; ++w)
-            G[w] = span_mask(SI, EI, w) & ~Nt[w];
-
-        uint32_t x[W];
-        int s = 0;
-        // Main diagonal: examined first for an early bound, ranked last.
+            z[w] = ~y[w] & span_mask(a, 32 * W - 1, w);
+        const int b = lowest(z) - 1;  // last column of the A_8 run
 #pragma unroll
         for (int w = 0; w < W; ++w)
-            x[w] = ~((Rh[w] ^ Th[w]) | (Rl[w] ^ Tl[w]) | Br[w]) & G[w];
-        int best_len = longest_run(x, 0, false, s);
-        int best_s = s;
-        bool best_main = best_len > 0;
-        for (int j = 1; j <= Ep; ++j) {
-            // upper_j: column c compares P[c - j] with T[c]
+            y[w] &= ~span_mask(a, b, w);
+        const int e = b + kLong - 1;  // last column of the run of x
+        const int L = e - a + 1;
+        if (st.nruns >= 0) {
+            if (st.nruns < kMaxRuns)
+                sk.runs[st.nruns++] = (uint32_t)a | ((uint32_t)e << 8) | ((uint32_t)slot << 16);
+            else
+                st.nruns = -1;
+        }
+        longest = max(longest, L);
+        if (beats_at(L, rank, a, best_len, best_rank, best_s)) {
+            best_len = L;
+            best_s = a;
+            best_rank = rank;
+        }
+    }
+    return longest;
+}
+
+// Solves the range on top of the stack (one call of Algorithm 4's EXEN
+// that extracts, or one that finds nothing).  Returns true once the pair is
+// finished: its stack is empty, it has made E+1 extractions, or it was
+// rejected by the first run's length.
+//
+// Work is arranged so that the lanes of a warp, each on its own pair, run
+// the same instructions: every diagonal first gets the cheap test for a run
+// of kLong columns (the same for all lanes), and only the few diagonals that
+// have such a run (usually one to three per similar pair, none for most
+// dissimilar pairs) get the full ladder, each lane walking its own list.  The
+// longest run of each diagonal over all columns is kept from the first
+// extraction and bounds it in every later one, where a diagonal that cannot
+// beat the best run so far is not examined.
+template <int W>
+__device__ __forceinline__ bool magnet_step(PairState<W> &st, PairStack &sk, int m)
+{
+    const uint32_t range = sk.range[--st.sp];
+    const int SI = (int)(range & 0xFFu), EI = (int)(range >> 8);
+    uint32_t G[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const uint32_t h = __funnelshift_l(w ? Rh[w ? w - 1 : 0] : 0u, Rh[w], j);
-                const uint32_t lo = __funnelshift_l(w ? Rl[w ? w - 1 : 0] : 0u, Rl[w], j);
-                const uint32_t b = __funnelshift_l(w ? Br[w ? w - 1 : 0] : 0xFFFFFFFFu, Br[w], j);
-                x[w] = ~((h ^ Th[w]) | (lo ^ Tl[w]) | b) & G[w];
-            }
-            int L = longest_run(x, best_len, best_main, s);
-            if (L) {
-                best_len = L;
-                best_s = s;
-                best_main = false;
-            }
-            // lower_j: column c compares P[c + j] with T[c]
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const int nx = w + 1 < W ? w + 1 : 0;
-                const uint32_t h = __funnelshift_r(Rh[w], w + 1 < W ? Rh[nx] : 0u, j);
-                const uint32_t lo = __funnelshift_r(Rl[w], w + 1 < W ? Rl[nx] : 0u, j);
-                const uint32_t b = __funnelshift_r(Br[w], w + 1 < W ? Br[nx] : 0xFFFFFFFFu, j);
-                x[w] = ~((h ^ Th[w]) | (lo ^ Tl[w]) | b) & G[w];
-            }
-            L = longest_run(x, best_len, best_main, s);
-            if (L) {
-                best_len = L;
-                best_s = s;
-                best_main = false;
+    for (int w = 0; w < W; ++w)
+        G[w] = span_mask(SI, EI, w) & ~st.Nt[w];
+    int best_len = 0, best_s = 0, best_rank = kMainRank + 1;
+    const bool first = st.done == 0;
+    const int range_len = EI - SI + 1;
+    // Later extractions: the listed long runs, clipped to the range.
+    if (!first && st.nruns > 0) {
+        for (int i = 0; i < st.nruns; ++i) {
+            const uint32_t r = sk.runs[i];
+            const int a = max((int)(r & 0xFFu), SI), e = min((int)((r >> 8) & 0xFFu), EI);
+            if (a > e)
+                continue;
+            const int rank = rank_of((int)(r >> 16));
+            if (beats_at(e - a + 1, rank, a, best_len, best_rank, best_s)) {
+                best_len = e - a + 1;
+                best_s = a;
+                best_rank = rank;
             }
         }
-        if (best_len == 0)
-            continue;  // no zero in the range: nothing extracted
-        if (done == 0 && best_len < first_min)
-            break;     // early rejection; the vector is still all ones
+    }
+    if (first || st.nruns < 0 || best_len < kLong) {
+        short_pass<W, 0>(st, sk, G, 0, first, range_len, best_len, best_s, best_rank);
+        for (int j = 1; j <= st.Ep; ++j) {
+            short_pass<W, 1>(st, sk, G, j, first, range_len, best_len, best_s, best_rank);
+            short_pass<W, -1>(st, sk, G, j, first, range_len, best_len, best_s, best_rank);
+        }
+    }
+    if (first || st.nruns < 0) {
+        for (uint64_t c = st.cand; c; c &= c - 1) {
+            const int slot = __ffsll((long long)c) - 1;
+            const int rank = rank_of(slot);
+            if (!first && !beats(sk.len[slot], rank, best_len, best_rank))
+                continue;
+            uint32_t x[W];
+            build_any(st, G, slot, x);
+            if (first && st.nruns >= 0) {
+                sk.len[slot] = (uint8_t)list_runs(st, sk, x, slot, best_len, best_s, best_rank);
+                continue;
+            }
+            int s = 0, k = 0;
+            // In the first extraction the exact length is kept as the bound
+            // for later ones, so it is taken even when it does not win.
+            const int L = longest_run(x, rank, first ? 0 : best_len,
+                                      first ? kMainRank + 1 : best_rank, s, k);
+            if (first)
+                sk.len[slot] = (uint8_t)L;
+            if (L > 0 && beats(L, rank, best_len, best_rank)) {
+                best_len = L;
+                best_s = s;
+                best_rank = rank;
+            }
+        }
+    }
+    if (best_len > 0) {
+        if (first && best_len < m / (st.Ep + 1)) {  // ceil((m - E) / (E + 1))
+            st.rejected = true;                     // the vector stays all ones
+            return true;
+        }
         const int e = best_s + best_len - 1;
 #pragma unroll
         for (int w = 0; w < W; ++w)
-            V[w] &= ~span_mask(best_s, e, w);
-        ++done;
-        if (best_s - 2 >= SI)
-            stack[sp++] = (uint16_t)(SI | ((best_s - 2) << 8));
-        if (e + 2 <= EI)
-            stack[sp++] = (uint16_t)((e + 2) | (EI << 8));
+            st.V[w] &= ~span_mask(best_s, e, w);
+        ++st.done;
+        if (best_s - 2 >= SI)  // left subproblem, solved after the right one
+            sk.range[st.sp++] = (uint16_t)(SI | ((best_s - 2) << 8));
+        if (e + 2 <= EI)       // right subproblem
+            sk.range[st.sp++] = (uint16_t)((e + 2) | (EI << 8));
     }
+    return st.sp == 0 || st.done > st.Ep;
+}
 
+template <int W>
+__device__ __forceinline__ int ones_of(const PairState<W> &st)
+{
     int ones = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w)
-        ones += __popc(V[w]);
-    const bool acc = live && ones <= Ep;
-    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, acc);
+        ones += __popc(st.V[w]);
+    return ones;
+}
+
+// One warp per group of 32 pairs, one lane per pair; the lanes take their
+// extractions in step (first extractions together, then second ones, ...),
+// which keeps them on the same code: a lane whose pair is finished waits.
+template <int W, bool WITH_N>
+__global__ void __launch_bounds__(kMagnetThreads)
+magnet_kernel(const FilterArgs a, const int E)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t g = (size_t)blockIdx.x * (kMagnetThreads / 32) + (threadIdx.x >> 5);
+    if (g >= groups_of(a.n_pairs))
+        return;  // whole warp
+    const int m = a.m;
+    const size_t pair = g * 32 + lane;
+    const bool live = pair < a.n_pairs;
+    uint32_t P[6][W];
+    load_group<W, WITH_N>(a, g, lane, P);
+    PairState<W> st;
+    PairStack sk;
+    init_pair(st, sk, P, m, a.E_per_pair && live ? min((int)__ldg(a.E_per_pair + pair), E) : E);
+    if (live)
+        while (!magnet_step(st, sk, m)) {
+        }
+    const int ones = ones_of(st);
+    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, live && ones <= st.Ep);
     if (lane == 0)
         a.accept[g] = bits;
     if (a.count && live)
         a.count[pair] = (uint8_t)ones;
     if (a.vectors) {
+        const size_t t = g / kLanes;
+        const int l = (int)(g % kLanes);
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const uint32_t col = warp_transpose(V[w], lane);
+            const uint32_t col = warp_transpose(live ? st.V[w] : 0u, lane);
             const int p = 32 * w + lane;
             if (p < m)
                 a.vectors[((size_t)t * m + p) * kLanes + l] = col;
@@ -333,8 +661,7 @@ template <int W>
 cudaError_t launch_W(const FilterArgs &a, int E, cudaStream_t s)
 {
     const size_t groups = groups_of(a.n_pairs);
-    const size_t warps_per_block = kMagnetThreads / 32;
-    const unsigned blocks = (unsigned)((groups + warps_per_block - 1) / warps_per_block);
+    const unsigned blocks = (unsigned)((groups + kMagnetThreads / 32 - 1) / (kMagnetThreads / 32));
     if (a.reads_n)
         magnet_kernel<W, true><<<blocks, kMagnetThreads, 0, s>>>(a, E);
     else

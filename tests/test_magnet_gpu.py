@@ -37,7 +37,12 @@ def _run(reads, refs, m, E, *, with_n, E_per_pair=None):
     ep = None if E_per_pair is None else torch.from_numpy(E_per_pair).to(dev)
     acc, cnt, vec = sj.shouji_magnet(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
                                      E_per_pair=ep, vectors=True)
+    # Without vectors: the same accept words and counts.
+    acc2, cnt2, _ = sj.shouji_magnet(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
+                                     E_per_pair=ep)
     torch.cuda.synchronize()
+    assert torch.equal(acc, acc2)
+    assert torch.equal(cnt[:n], cnt2[:n])
     return (_bits(acc, n), cnt[:n].cpu().numpy(),
             vec.cpu().numpy().view(np.uint32), acc.cpu().numpy().view(np.uint32))
 
@@ -83,6 +88,25 @@ def test_magnet_edge_cases():
             refs[40:50] = rng.choice(np.frombuffer(b"GT", np.uint8), size=(10, m))
             reads[40:50] = rng.choice(np.frombuffer(b"AC", np.uint8), size=(10, m))  # disjoint
             refs[50:70, :] = np.roll(reads[50:70], 1 + (m // 7), axis=1)  # shifted copies
+            bits, cnt, vec, _ = _run(reads, refs, m, E, with_n=False)
+            _check(reads, refs, m, E, bits, cnt, vec)
+
+
+def test_magnet_many_long_runs():
+    """Pairs with more runs of 8 or more matching columns than the kernel lists
+    (a read of one letter against a reference with a mismatch every 9
+    columns: every diagonal then has a run of 8 between each two mismatches)."""
+    rng = np.random.default_rng(12)
+    for m in (100, 255):
+        for E in (2, 5, 31):
+            n = 64
+            reads = np.full((n, m), ord("A"), np.uint8)
+            refs = np.full((n, m), ord("A"), np.uint8)
+            for i in range(n):
+                period = 9 + (i % 4)
+                refs[i, (i % period)::period] = ord("C")
+                if i % 3 == 0:  # a few extra differences
+                    refs[i, rng.integers(0, m, size=3)] = ord("G")
             bits, cnt, vec, _ = _run(reads, refs, m, E, with_n=False)
             _check(reads, refs, m, E, bits, cnt, vec)
 

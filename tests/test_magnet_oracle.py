@@ -118,3 +118,17 @@ def test_planted_mistake_fails_a_pin(name, tmp_path):
     magnet = _build(name, MUTANTS[name], tmp_path)
     failed = [p.__name__ for p in ALL_MAGNET_PINS if not p(magnet)]
     assert failed, "planted mistake %s passes every MAGNET pin" % name
+
+
+def test_batch_matches_single_calls():
+    """The threaded batch entry gives, pair by pair, the single-pair results."""
+    rng = np.random.default_rng(21)
+    n, m, E = 300, 60, 4
+    reads = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=(n, m))
+    refs = reads.copy()
+    mut = rng.random((n, m)) < 0.06
+    refs[mut] = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=int(mut.sum()))
+    acc, cnt = oracle.shouji_batch(reads, refs, E, threads=3, magnet=True)
+    for i in range(n):
+        _, c = oracle.magnet(reads[i].tobytes(), refs[i].tobytes(), E)
+        assert cnt[i] == c and acc[i] == (c <= E)
