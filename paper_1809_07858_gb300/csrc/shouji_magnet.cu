@@ -450,6 +450,89 @@ __device__ __forceinline__ void short_pass(PairState<W> &st, PairStack &sk,
     }
 }
 
+// Word idx of a column mask, picked at a run-time index without indexing
+// the register array (fill outside [0, W)).
+template <int W>
+__device__ __forceinline__ uint32_t word_at(const uint32_t (&P)[W], int idx, uint32_t fill)
+{
+    uint32_t v = fill;
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        v = (w == idx) ? P[w] : v;
+    return v;
+}
+
+// The columns of a later range that lies inside two words (ws, ws+1): the
+// reference words there, the read words one word further on each side (a
+// diagonal moves the read by up to 31 columns), and the range mask.
+struct Window {
+    uint32_t Rh[4], Rl[4], Br[4];  // read words ws-1 .. ws+2
+    uint32_t Th[2], Tl[2], G[2];   // reference words ws, ws+1; range and N mask
+    int base;                      // first column of word ws
+};
+
+template <int W>
+__device__ __forceinline__ void make_window(const PairState<W> &st, int SI, int EI, Window &win)
+{
+    const int ws = SI >> 5;
+    win.base = 32 * ws;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        win.Rh[k] = word_at(st.Rh, ws - 1 + k, 0u);
+        win.Rl[k] = word_at(st.Rl, ws - 1 + k, 0u);
+        win.Br[k] = word_at(st.Br, ws - 1 + k, 0xFFFFFFFFu);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        win.Th[k] = word_at(st.Th, ws + k, 0u);
+        win.Tl[k] = word_at(st.Tl, ws + k, 0u);
+        win.G[k] = span_mask(SI - win.base, EI - win.base, k) & ~word_at(st.Nt, ws + k, 0u);
+    }
+}
+
+// short_pass for a later range inside a window: the same test on two words.
+template <int DIR>
+__device__ __forceinline__ void window_pass(const Window &win, uint64_t cand, const PairStack &sk,
+                                            int j, int range_len, int &best_len, int &best_s,
+                                            int &best_rank)
+{
+    const int slot = DIR > 0 ? 2 * j - 1 : DIR < 0 ? 2 * j : 0;
+    const int rank = rank_of(slot);
+    const bool is_cand = ((cand >> slot) & 1ull) != 0;
+    const int ub = min(is_cand ? kLong - 1 : (int)sk.len[slot], range_len);
+    if (ub < best_len || (ub == best_len && rank > best_rank))
+        return;
+    uint32_t x[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        uint32_t h, lo, b;
+        if (DIR > 0) {  // read words ws+k-1, ws+k moved up by j
+            h = __funnelshift_l(win.Rh[k], win.Rh[k + 1], j);
+            lo = __funnelshift_l(win.Rl[k], win.Rl[k + 1], j);
+            b = __funnelshift_l(win.Br[k], win.Br[k + 1], j);
+        } else if (DIR < 0) {  // read words ws+k, ws+k+1 moved down by j
+            h = __funnelshift_r(win.Rh[k + 1], win.Rh[k + 2], j);
+            lo = __funnelshift_r(win.Rl[k + 1], win.Rl[k + 2], j);
+            b = __funnelshift_r(win.Br[k + 1], win.Br[k + 2], j);
+        } else {
+            h = win.Rh[k + 1];
+            lo = win.Rl[k + 1];
+            b = win.Br[k + 1];
+        }
+        x[k] = ~((h ^ win.Th[k]) | (lo ^ win.Tl[k]) | b) & win.G[k];
+    }
+    int s = 0;
+    const int L = short_run(x, s);
+    if (L <= 0)
+        return;  // no zero, or (impossible here) a run of kLong
+    s += win.base;
+    if (beats_at(L, rank, s, best_len, best_rank, best_s)) {
+        best_len = L;
+        best_s = s;
+        best_rank = rank;
+    }
+}
+
 // Lowest set bit of a column mask (32 W when empty).
 template <int W>
 __device__ __forceinline__ int lowest(const uint32_t (&y)[W])
@@ -555,7 +638,17 @@ __device__ __forceinline__ bool magnet_step(PairState<W> &st, PairStack &sk, int
             }
         }
     }
-    if (first || st.nruns < 0 || best_len < kLong) {
+    if (W > 2 && !first && st.nruns >= 0 && best_len < kLong && EI < 32 * (SI >> 5) + 64) {
+        // A later range inside two words (nearly all of them): the test on
+        // the two words only.
+        Window win;
+        make_window(st, SI, EI, win);
+        window_pass<0>(win, st.cand, sk, 0, range_len, best_len, best_s, best_rank);
+        for (int j = 1; j <= st.Ep; ++j) {
+            window_pass<1>(win, st.cand, sk, j, range_len, best_len, best_s, best_rank);
+            window_pass<-1>(win, st.cand, sk, j, range_len, best_len, best_s, best_rank);
+        }
+    } else if (first || st.nruns < 0 || best_len < kLong) {
         short_pass<W, 0>(st, sk, G, 0, first, range_len, best_len, best_s, best_rank);
         for (int j = 1; j <= st.Ep; ++j) {
             short_pass<W, 1>(st, sk, G, j, first, range_len, best_len, best_s, best_rank);
