@@ -482,6 +482,10 @@ def run_ours(args, world, rank, local):
         rate = cpu_oracle_rate(h_reads[:sample].numpy(), h_refs[:sample].numpy(), threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "pairs 0..%d of the same workload (%d threads)" % (sample - 1, threads)}
+        one = max(1, sample // 10)
+        cpu["single_thread"] = {
+            "value": cpu_oracle_rate(h_reads[:one].numpy(), h_refs[:one].numpy(), 1),
+            "unit": UNIT, "sample": "pairs 0..%d, one thread" % (one - 1)}
         if magnet is not None:
             msample = max(1, sample // 10)
             mrate = cpu_oracle_rate(h_reads[:msample].numpy(), h_refs[:msample].numpy(), threads,
