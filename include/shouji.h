@@ -251,7 +251,7 @@ shouji_status shouji_compact(const uint32_t *accept, size_t n_pairs,
  * synchronize the device.  It allocates nothing and calls no allocating
  * routine.
  *
- * Its workspace is a fixed 16 KB __device__ array inside libshouji.so, held
+ * Its workspace is a fixed 64 KB __device__ array inside libshouji.so, held
  * on every GPU that loads the library until the process exits.  The first
  * call on each device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call

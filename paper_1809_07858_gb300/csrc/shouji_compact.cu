@@ -3,12 +3,14 @@
 // The paper's accelerator returns one result bit per pair, in input order,
 // and the host picks the pairs that go on to alignment (Sec. 2.3).  Here the
 // selection runs on the device in three launches over the accept bit-mask:
-//   1. count:  each CTA sums the popcounts of its 4096-word slice;
+//   1. count:  each CTA sums the popcounts of its 1024-word slice;
 //   2. scan:   one CTA turns the per-slice sums into exclusive offsets and
 //              writes the total (the workspace holds one uint32 per slice);
-//   3. write:  each CTA re-reads its slice, ranks every word with a warp
-//              shuffle scan plus a CTA scan over warps, and every thread
-//              writes the indices of the set bits of its words in order.
+//   3. write:  each CTA re-reads its slice and ranks every thread's four
+//              words with a CTA scan; then each warp walks its 128 words in
+//              order, and for each word its lanes write the indices of the
+//              word's set bits with one coalesced store (lane b writes bit b
+//              at the word's offset plus the bits below b).
 // No CTA waits on another, so nothing can spin.
 #include "shouji_internal.cuh"
 
@@ -16,8 +18,8 @@ namespace shouji {
 namespace {
 
 constexpr int kCThreads = 256;
-constexpr int kWordsPerThread = 16;
-constexpr int kSliceWords = kCThreads * kWordsPerThread;  // 4096 words = 131072 pairs
+constexpr int kWordsPerThread = kCompactSliceWords / kCThreads;  // 4
+constexpr int kSliceWords = kCompactSliceWords;                  // 1024 words = 32768 pairs
 
 __device__ __forceinline__ uint32_t load_word(const uint32_t *accept, size_t wi,
                                               size_t n_words, size_t n_pairs)
@@ -106,27 +108,38 @@ compact_write(const uint32_t *__restrict__ accept, size_t n_pairs, size_t n_word
               const uint32_t *__restrict__ slice_offsets, uint32_t *__restrict__ out_idx,
               uint32_t pair_base)
 {
-    // Thread t owns words w0 + t*16 .. w0 + t*16 + 15 (consecutive), so the
-    // order of threads is the order of pairs.
+    // Thread t owns words w0 + 4t .. w0 + 4t + 3 (consecutive), so the order
+    // of threads is the order of pairs.
+    const int lane = threadIdx.x & 31;
     const size_t w0 = (size_t)blockIdx.x * kSliceWords + (size_t)threadIdx.x * kWordsPerThread;
-    uint32_t words[kWordsPerThread];
+    uint32_t words[kWordsPerThread], at[kWordsPerThread];
     uint32_t c = 0;
 #pragma unroll
     for (int i = 0; i < kWordsPerThread; ++i) {
         words[i] = load_word(accept, w0 + i, n_words, n_pairs);
+        at[i] = c;
         c += __popc(words[i]);
     }
     uint32_t total;
     const uint32_t inc = cta_inclusive_scan(c, &total);
-    uint32_t pos = slice_offsets[blockIdx.x] + inc - c;
+    const uint32_t pos = slice_offsets[blockIdx.x] + inc - c;
 #pragma unroll
-    for (int i = 0; i < kWordsPerThread; ++i) {
-        uint32_t w = words[i];
-        const uint32_t pair0 = pair_base + (uint32_t)((w0 + i) * 32);
-        while (w) {
-            const int b = __ffs(w) - 1;
-            out_idx[pos++] = pair0 + (uint32_t)b;
-            w &= w - 1;
+    for (int i = 0; i < kWordsPerThread; ++i)
+        at[i] += pos;
+    // Word by word across the warp, in pair order: owner lane o, word i.
+    const uint32_t below = (1u << lane) - 1u;
+    const size_t warp_w0 = w0 - (size_t)lane * kWordsPerThread;
+    for (int o = 0; o < 32; ++o) {
+#pragma unroll
+        for (int i = 0; i < kWordsPerThread; ++i) {
+            const uint32_t w = __shfl_sync(0xFFFFFFFFu, words[i], o);
+            if (!w)
+                continue;
+            const uint32_t base = __shfl_sync(0xFFFFFFFFu, at[i], o);
+            if ((w >> lane) & 1u)
+                out_idx[base + __popc(w & below)] =
+                    pair_base + (uint32_t)((warp_w0 + (size_t)o * kWordsPerThread + i) * 32) +
+                    (uint32_t)lane;
         }
     }
 }

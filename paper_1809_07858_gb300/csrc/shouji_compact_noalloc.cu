@@ -2,7 +2,7 @@
 // cudaMalloc.
 //
 // shouji_compact needs a small device workspace (one uint32 per slice of
-// 131072 pairs) that the caller allocates.  Some callers have no way to do
+// 32768 pairs) that the caller allocates.  Some callers have no way to do
 // that: a host program whose device memory is owned by another allocator
 // (a framework's pool with a fixed budget, an embedding application that
 // hands this library only its input and output buffers), or a latency-bound
@@ -23,7 +23,9 @@ namespace shouji {
 namespace {
 
 constexpr int kNoallocMaxDevices = 64;
-constexpr size_t kNoallocMaxSlices = 4096;  // 16 KB: up to 4096 * 131072 pairs
+// 64 KB: one uint32 per slice of 32 * kCompactSliceWords pairs, up to
+// SHOUJI_NOALLOC_MAX_PAIRS pairs.
+constexpr size_t kNoallocMaxSlices = SHOUJI_NOALLOC_MAX_PAIRS / (32 * (size_t)kCompactSliceWords);
 
 static __device__ __align__(256) uint32_t g_compact_scratch[kNoallocMaxSlices];
 

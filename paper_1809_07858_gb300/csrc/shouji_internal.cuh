@@ -39,6 +39,9 @@ cudaError_t launch_filter(const FilterArgs &a, int E, cudaStream_t s);
 template <int E>
 cudaError_t launch_filter_E(const FilterArgs &a, cudaStream_t s);
 
+// Compaction works on slices of kCompactSliceWords accept words (32 pairs
+// each); its workspace holds one uint32 per slice.
+constexpr int kCompactSliceWords = 1024;
 size_t compact_workspace_bytes(size_t n_pairs);
 cudaError_t launch_compact(const uint32_t *accept, size_t n_pairs,
                            uint32_t *out_idx, uint32_t *out_n, void *workspace,

@@ -214,7 +214,7 @@ def test_nonzero_stream_and_zero_pairs():
 
 
 # ---------------------------------------------------------------- compact
-@pytest.mark.parametrize("n", [1, 31, 32, 33, 1000, 131072, 131073, 5_000_001])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 1000, 32768, 32769, 131072, 131073, 5_000_001])
 @pytest.mark.parametrize("density", [0.0, 0.03, 0.5, 1.0])
 def test_compact_matches_flatnonzero(n, density):
     rng = np.random.default_rng(n)
