@@ -298,15 +298,9 @@ pack_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int max_m,
 // cp.async while the current block is transposed, so the gathers' memory
 // latency overlaps the transposition.  Padding slots are zero-filled by the
 // copy itself (source size 0).
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, uint32_t src_bytes)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+using packdev::cp_async16;
+using packdev::cp_async_commit;
+using packdev::cp_async_wait;
 
 struct PackBlock {
     int m, rs;

@@ -7,7 +7,9 @@
 // ASCII byte: A=00, C=01, G=11, T=10 (hi, lo); 'N' is flagged separately.
 //
 // One CTA of 256 threads packs 256 sequences = 8 lanes of a 1024-sequence
-// tile.  Phase 1 copies the CTA's rows into shared memory as one dense block
+// tile (for contiguous rows on a 16-byte boundary, a persistent CTA walks
+// such blocks with double buffering; see pack_stream_kernel).  Phase 1
+// copies the CTA's rows into shared memory as one dense block
 // (row r at byte r*m).  When the rows are contiguous in global memory
 // (stride == m) the block is a single contiguous range and is copied with
 // 16-byte (or 4-byte) loads, four in flight per thread; otherwise row by
@@ -100,6 +102,95 @@ pack_kernel(const uint8_t *__restrict__ seqs, uint64_t stride, size_t n, int m,
     pack_transpose<WITH_N, ALIGNED>(sm, m, m, tile, lane0, packed, nmask, rot_step, kPackThreads);
 }
 
+// Contiguous rows on a 16-byte boundary (the common case): a persistent,
+// double-buffered form.  Each CTA walks blocks blockIdx.x, +gridDim.x, ...;
+// while it transposes block i from one buffer, the 16-byte chunks of block
+// i+1 are already on their way into the other with cp.async, so the loads of
+// the next block overlap the transposition of this one.  A chunk past the
+// CTA's rows is zero-filled by the copy itself (source size 0); the last
+// partial chunk copies only its valid bytes.
+template <bool WITH_N, bool ALIGNED>
+__global__ void __launch_bounds__(kPackThreads)
+pack_stream_kernel(const uint8_t *__restrict__ seqs, size_t n, int m,
+                   uint32_t *__restrict__ packed, uint32_t *__restrict__ nmask, int rot_step,
+                   size_t n_blocks, int buf_bytes)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint8_t *bufs = reinterpret_cast<uint8_t *>(sm);
+    const int tid = threadIdx.x;
+    const int chunks = buf_bytes >> 4;
+
+    auto issue = [&](size_t blk, uint8_t *dst) {
+        const size_t seq0 = blk * kPackSeqs;
+        // blocks of the last tile may start at or past n: they stage no rows
+        const size_t left = seq0 < n ? n - seq0 : 0;
+        const int rows = (int)(left < (size_t)kPackSeqs ? left : (size_t)kPackSeqs);
+        const int nbytes = rows * m;
+        const uint8_t *src = seqs + seq0 * (size_t)m;
+        for (int k = tid; k < chunks; k += kPackThreads) {
+            const int rem = nbytes - 16 * k;
+            const uint32_t bytes = rem >= 16 ? 16u : rem > 0 ? (uint32_t)rem : 0u;
+            cp_async16(dst + 16 * k, bytes ? src + 16 * k : seqs, bytes);
+        }
+    };
+
+    size_t blk = blockIdx.x;
+    if (blk < n_blocks)
+        issue(blk, bufs);
+    cp_async_commit();
+    for (int i = 0; blk < n_blocks; ++i, blk += gridDim.x) {
+        const size_t next = blk + gridDim.x;
+        if (next < n_blocks)
+            issue(next, bufs + (size_t)((i + 1) & 1) * buf_bytes);
+        cp_async_commit();  // possibly empty: keeps one group per block
+        cp_async_wait<1>();  // this thread's copies of block blk are in
+        __syncthreads();    // and everyone's
+        const size_t seq0 = blk * kPackSeqs;
+        pack_transpose<WITH_N, ALIGNED>(
+            reinterpret_cast<const uint32_t *>(bufs + (size_t)(i & 1) * buf_bytes), m, m,
+            seq0 / kTile, (int)((seq0 % kTile) / 32), packed, nmask, rot_step, kPackThreads);
+        __syncthreads();    // the buffer may be refilled
+    }
+    cp_async_wait<0>();
+}
+
+template <bool WITH_N, bool ALIGNED>
+cudaError_t launch_stream_ta(const uint8_t *seqs, size_t n, int m, uint32_t *packed,
+                             uint32_t *nmask, int rot, cudaStream_t s)
+{
+    // one buffer: 256 rows of m bytes and 16 bytes of zero padding, in
+    // whole 16-byte chunks
+    const int buf_bytes = (kPackSeqs * m + 16 + 15) / 16 * 16;
+    const size_t smem = 2 * (size_t)buf_bytes;
+    const size_t n_blocks = tiles_of(n) * (kTile / kPackSeqs);
+    cudaError_t e = cudaFuncSetAttribute(pack_stream_kernel<WITH_N, ALIGNED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+             &per_sm, pack_stream_kernel<WITH_N, ALIGNED>, kPackThreads, smem)) != cudaSuccess)
+        return e;
+    const size_t full = (size_t)sms * (per_sm > 0 ? per_sm : 1);
+    const unsigned grid = (unsigned)(n_blocks < full ? n_blocks : full);
+    pack_stream_kernel<WITH_N, ALIGNED><<<grid, kPackThreads, smem, s>>>(
+        seqs, n, m, packed, nmask, rot, n_blocks, buf_bytes);
+    return cudaGetLastError();
+}
+
+template <bool WITH_N>
+cudaError_t launch_stream_t(const uint8_t *seqs, size_t n, int m, uint32_t *packed,
+                            uint32_t *nmask, int rot, cudaStream_t s)
+{
+    if (m % 4 == 0)
+        return launch_stream_ta<WITH_N, true>(seqs, n, m, packed, nmask, rot, s);
+    return launch_stream_ta<WITH_N, false>(seqs, n, m, packed, nmask, rot, s);
+}
+
 template <bool WITH_N>
 cudaError_t launch_pack_t(const uint8_t *seqs, uint64_t stride, size_t n, int m,
                           uint32_t *packed, uint32_t *nmask, cudaStream_t s)
@@ -115,6 +206,8 @@ cudaError_t launch_pack_t(const uint8_t *seqs, uint64_t stride, size_t n, int m,
     }
     const int rot = rotation_step(m);
     cudaError_t e;
+    if (mode == kCopyVec16)
+        return launch_stream_t<WITH_N>(seqs, n, m, packed, nmask, rot, s);
     if (m % 4 == 0) {
         e = cudaFuncSetAttribute(pack_kernel<WITH_N, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -103,5 +103,19 @@ __host__ __device__ inline int rotation_step(int rs, int lanes = 8)
     return 0;
 }
 
+// 16-byte global -> shared copies that run while the thread goes on
+// (cp.async); a source size below 16 zero-fills the rest of the 16 bytes, and
+// a size of 0 reads nothing.  wait<N> waits for this thread's copies of all
+// but the N most recent groups.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, uint32_t src_bytes)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 }  // namespace packdev
 }  // namespace shouji
