@@ -156,3 +156,44 @@ def test_magnet_full_size():
     assert bad.size == 0, "%d pairs differ, first %s" % (bad.size, bad[:10])
     del pr, pt, acc
     torch.cuda.empty_cache()
+
+
+def test_magnet_random_configurations():
+    """Random lengths, thresholds, N densities, alphabets and per-pair
+    thresholds, every pair's count and accept bit against the oracle."""
+    dev = _dev()
+    rng = np.random.default_rng(2024)
+    for trial in range(40):
+        m = int(rng.choice([int(rng.integers(1, 256)), 100, 150, 250]))
+        E = int(rng.integers(0, 32))
+        n = int(rng.integers(1, 3000))
+        alphabet = np.frombuffer(rng.choice([b"ACGT", b"AC", b"AAAC", b"ACGTN"]), np.uint8)
+        reads = rng.choice(alphabet, size=(n, m)).astype(np.uint8)
+        refs = reads.copy()
+        # near pairs: a few substitutions and shifts; far pairs: random
+        k = rng.integers(0, max(1, E + 3), size=n)
+        for i in range(n):
+            if rng.random() < 0.3:
+                refs[i] = rng.choice(alphabet, size=m)
+                continue
+            for _ in range(int(k[i])):
+                pos = int(rng.integers(0, m))
+                if rng.random() < 0.6:
+                    refs[i, pos] = rng.choice(alphabet)
+                else:
+                    refs[i, pos:] = np.roll(refs[i, pos:], 1 if rng.random() < 0.5 else -1)
+        with_n = bool((reads == ord("N")).any() or (refs == ord("N")).any() or rng.random() < 0.3)
+        ep = rng.integers(0, E + 2, size=n).astype(np.uint8) if rng.random() < 0.3 else None
+        pr, nr = sj.shouji_pack(torch.from_numpy(reads).to(dev), m, with_n=with_n)
+        pt, nt = sj.shouji_pack(torch.from_numpy(refs).to(dev), m, with_n=with_n)
+        acc, cnt, _ = sj.shouji_magnet(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
+                                       E_per_pair=None if ep is None else torch.from_numpy(ep).to(dev))
+        torch.cuda.synchronize()
+        bits, cnt = _bits(acc, n), cnt[:n].cpu().numpy()
+        # without N masks an 'N' is read as 'G'
+        r_o = reads if with_n else np.where(reads == ord("N"), ord("G"), reads).astype(np.uint8)
+        t_o = refs if with_n else np.where(refs == ord("N"), ord("G"), refs).astype(np.uint8)
+        e_o = None if ep is None else np.minimum(ep, E).astype(np.uint8)
+        acc_o, cnt_o = oracle.shouji_batch(r_o, t_o, E, E_per_pair=e_o, threads=8, magnet=True)
+        bad = np.flatnonzero((cnt != cnt_o) | (bits != acc_o))
+        assert bad.size == 0, (trial, m, E, n, with_n, ep is not None, bad[:5])
