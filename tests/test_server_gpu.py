@@ -76,6 +76,11 @@ def test_wait_deadline_and_memory_bounded_slots():
     one = sj.Server(400_000, 250, 2, 12, max_stride=256, max_slots=8)
     _, per_slot = one.info()
     one.close()
+    # a budget below one slot admits nothing: SHOUJI_ENOMEM, and nothing is kept
+    with pytest.raises(sj.ShoujiError) as err:
+        sj.Server(400_000, 250, 2, 12, max_stride=256, max_slots=8,
+                  memory_budget=per_slot // 2)
+    assert err.value.status == 2
     # a budget for two slots gives two slots
     srv = sj.Server(400_000, 250, 2, 12, max_stride=256, max_slots=8,
                     memory_budget=int(2.5 * per_slot))
