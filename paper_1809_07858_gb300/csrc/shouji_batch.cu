@@ -227,69 +227,73 @@ pack_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int max_m,
 {
     extern __shared__ __align__(16) uint32_t sm[];
     uint8_t *sb = reinterpret_cast<uint8_t *>(sm);
-    const uint32_t blk = blockIdx.x;
-    const uint32_t nmc = T->n_mc;
-    if (nmc == 0 || blk >= T->mc_block[nmc])
-        return;
-    uint32_t lo = 0, hi = nmc;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (T->mc_block[mid] <= blk)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    const int m = (int)T->mc_m[lo];
-    const uint32_t rel = (blk - T->mc_block[lo]) * kPackSeqs;  // slot offset in the m-class
-    const uint32_t slot0 = T->mc_slot[lo] + rel;
     const uint8_t *seqs = blockIdx.y ? a->refs : a->reads;
     const uint64_t stride = a->stride;
     // rows on 16-byte boundaries are packed by pack_async_kernel instead
     if (rows_on_16_bytes(seqs, stride, max_m))
         return;
+    const uint32_t nmc = T->n_mc;
+    if (nmc == 0)
+        return;
+    const uint32_t total = T->mc_block[nmc];
+    // the CTAs walk the blocks blockIdx.x, +gridDim.x, ...
+    for (uint32_t blk = blockIdx.x; blk < total; blk += gridDim.x) {
+        uint32_t lo = 0, hi = nmc;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (T->mc_block[mid] <= blk)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const int m = (int)T->mc_m[lo];
+        const uint32_t rel = (blk - T->mc_block[lo]) * kPackSeqs;  // slot offset in the m-class
+        const uint32_t slot0 = T->mc_slot[lo] + rel;
 
-    // Phase 1: gather the 128 rows (zeros for padding slots) into sm, row r at
-    // byte r * rs, as bytes, 8 rows per warp at a time.
-    const int rs = row_stride(m);
-    {
-        const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-        for (int rb = 0; rb < 32; rb += 8) {
-            const int r0 = warp * 32 + rb;
-            uint32_t pair[8];
+        // Phase 1: gather the 128 rows (zeros for padding slots) into sm, row r
+        // at byte r * rs, as bytes, 8 rows per warp at a time.
+        const int rs = row_stride(m);
+        {
+            const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+            for (int rb = 0; rb < 32; rb += 8) {
+                const int r0 = warp * 32 + rb;
+                uint32_t pair[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                pair[k] = perm[slot0 + r0 + k];
-            uint8_t v[8][8];
+                for (int k = 0; k < 8; ++k)
+                    pair[k] = perm[slot0 + r0 + k];
+                uint8_t v[8][8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint8_t *src = seqs + (uint64_t)(pair[k] == kNoPair ? 0 : pair[k]) * stride;
-                const bool ok = pair[k] != kNoPair;
+                for (int k = 0; k < 8; ++k) {
+                    const uint8_t *src = seqs + (uint64_t)(pair[k] == kNoPair ? 0 : pair[k]) * stride;
+                    const bool ok = pair[k] != kNoPair;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = ln + 32 * q;
-                    v[k][q] = (ok && j < m) ? __ldg(src + j) : (uint8_t)0;
+                    for (int q = 0; q < 8; ++q) {
+                        const int j = ln + 32 * q;
+                        v[k][q] = (ok && j < m) ? __ldg(src + j) : (uint8_t)0;
+                    }
                 }
-            }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                uint8_t *dst = sb + (r0 + k) * rs;
+                for (int k = 0; k < 8; ++k) {
+                    uint8_t *dst = sb + (r0 + k) * rs;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = ln + 32 * q;
-                    if (j < m)
-                        dst[j] = v[k][q];
+                    for (int q = 0; q < 8; ++q) {
+                        const int j = ln + 32 * q;
+                        if (j < m)
+                            dst[j] = v[k][q];
+                    }
                 }
             }
         }
-    }
-    __syncthreads();
+        __syncthreads();
 
-    const size_t tile = rel / kTile;
-    const int lane0 = (int)((rel % kTile) / 32);
-    uint32_t *packed = reinterpret_cast<uint32_t *>((blockIdx.y ? prefs : preads) + T->mc_poff[lo]);
-    uint32_t *nmask = WITH_N ? (blockIdx.y ? nrefs : nreads) + T->mc_poff[lo] : nullptr;
-    packdev::pack_transpose<WITH_N, true, kPackLanes>(
-        sm, m, rs, tile, lane0, packed, nmask, packdev::rotation_step(rs, kPackLanes), kPackThreads);
+        const size_t tile = rel / kTile;
+        const int lane0 = (int)((rel % kTile) / 32);
+        uint32_t *packed = reinterpret_cast<uint32_t *>((blockIdx.y ? prefs : preads) + T->mc_poff[lo]);
+        uint32_t *nmask = WITH_N ? (blockIdx.y ? nrefs : nreads) + T->mc_poff[lo] : nullptr;
+        packdev::pack_transpose<WITH_N, true, kPackLanes>(
+            sm, m, rs, tile, lane0, packed, nmask, packdev::rotation_step(rs, kPackLanes), kPackThreads);
+        __syncthreads();  // sm is refilled for the next block
+    }
 }
 
 // The same pack as a persistent, double-buffered kernel for rows that start on
@@ -460,6 +464,7 @@ struct shouji_batch {
     int e_lo = 0, e_hi = 0, with_n = 0;
     size_t slots_cap = 0;
     size_t pack_blocks_cap = 0;
+    int pack_grid = 0;      // CTAs per side of the fallback pack (walks the blocks)
     int async_grid = 0;     // CTAs per side of the persistent pack (0: not used)
     int async_buf = 0;      // bytes of one shared-memory buffer
     Args *d_args = nullptr, *h_args = nullptr;
@@ -556,7 +561,7 @@ cudaError_t enqueue_prologue(shouji_batch *b, cudaStream_t s)
     // The persistent double-buffered pack needs rows on 16-byte boundaries;
     // the stride is known only per run, so both forms are in the graph and
     // each exits at once when the other one applies.
-    const dim3 pgrid((unsigned)b->pack_blocks_cap, 2);
+    const dim3 pgrid((unsigned)b->pack_grid, 2);
     const dim3 agrid((unsigned)b->async_grid, 2);
     if (b->with_n) {
         pack_kernel<true><<<pgrid, kPackThreads, pack_smem(b->max_m), s>>>(
@@ -763,6 +768,10 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, i
     b->slots_cap = (max_pairs + (size_t)kBins * 31 + (size_t)(kMaxM - 1) * (kTile - 1) + kTile - 1) /
                    kTile * kTile;
     b->pack_blocks_cap = b->slots_cap / kPackSeqs;
+    b->pack_grid = (int)(b->pack_blocks_cap < (size_t)b->sms * 8 ? b->pack_blocks_cap
+                                                                  : (size_t)b->sms * 8);
+    if (b->pack_grid < 1)
+        b->pack_grid = 1;
     const size_t packed_u2 = b->slots_cap / kTile * max_m * kLanes;  // uint2 per side
     bool ok = true;
     ok = ok && cudaMalloc(&b->d_args, sizeof(Args)) == cudaSuccess;
