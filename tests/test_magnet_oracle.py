@@ -33,7 +33,7 @@ def test_hand_case(case):
 
 
 def test_fig6c_local_parity_unpinned():
-    """Fig. 6(c): the figure labels MAGNET's local result "4 edits"; the readings
+    """Fig. 6(c): the figure labels MAGNET's local result as 4 edits; the readings
     taken here give 5 (the Shouji count of the same example is also one above
     its label).  Kept as a regression value, not a pin."""
     g = read_kv("fig6c.txt")
