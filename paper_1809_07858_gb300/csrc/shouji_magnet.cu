@@ -44,7 +44,7 @@
 namespace shouji {
 namespace {
 
-constexpr int kMagnetThreads = 128;
+constexpr int kMagnetThreads = 64;
 constexpr int kMaxStack = SHOUJI_MAX_E + 3;  // 1 + one net push per extraction
 constexpr int kMainRank = 2 * SHOUJI_MAX_E;  // after every upper_j and lower_j
 constexpr int kLong = 8;                     // runs this long are listed
