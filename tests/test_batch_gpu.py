@@ -135,3 +135,33 @@ def test_unaligned_stride_byte_path():
     acc_o, cnt_o = oracle_mixed(reads, refs, lens, Es)
     assert (cnt == cnt_o).all() and (acc == acc_o).all()
     b.close()
+
+
+@pytest.mark.slow
+def test_full_size_batch_sampled():
+    """The benchmark's batched workload at its full size (50M pairs, lengths
+    40% 100 / 40% 150 / 20% 250, E uniform in 2..12, unsorted, stride 256) in one
+    graph launch: properties over every pair, and a seeded sample of 300k pairs
+    against the oracle."""
+    d = dev()
+    n = 50_000_000
+    lens, Es = synth.mixed_shape(n, seed=4242)
+    reads, refs = synth.pairs(n, 250, seed=4242, near=(0, 6), far=(7, 40), far_fraction=0.5,
+                              lengths=lens, stride=256)
+    b = sj.Batch(n, 250, 2, 12)
+    acc, cnt = b.run(torch.from_numpy(reads).to(d), torch.from_numpy(refs).to(d),
+                     torch.from_numpy(lens.astype(np.int16)).to(d), torch.from_numpy(Es).to(d))
+    torch.cuda.synchronize()
+    invalid = b.invalid()
+    b.close()
+    bits = accept_bits(acc.cpu().numpy(), n)
+    cnt = cnt[:n].cpu().numpy()
+    assert invalid == 0
+    assert (cnt <= lens).all()
+    assert (bits == (cnt <= Es)).all()
+    pick = np.sort(np.random.default_rng(50).choice(n, size=300_000, replace=False))
+    acc_o, cnt_o = oracle_mixed(reads[pick], refs[pick], lens[pick], Es[pick])
+    assert (cnt[pick] == cnt_o).all()
+    assert (bits[pick] == acc_o).all()
+    del acc
+    torch.cuda.empty_cache()
