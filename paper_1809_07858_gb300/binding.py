@@ -26,7 +26,7 @@ __all__ = [
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
     "Batch", "Server", "shouji_count", "COUNT_GLOBAL", "COUNT_LOCAL", "COUNT_GLOCAL_START",
-    "COUNT_GLOCAL_END", "shouji_magnet",
+    "COUNT_GLOCAL_END", "shouji_magnet", "magnet_pairs",
 ]
 
 COUNT_GLOBAL, COUNT_LOCAL, COUNT_GLOCAL_START, COUNT_GLOCAL_END = 0, 1, 2, 3
@@ -301,6 +301,23 @@ def filter_pairs(reads, refs, E: int, *, with_n: bool | None = None, E_per_pair=
     pr, nr = shouji_pack(reads, m, with_n=with_n, stream=stream)
     pt, nt = shouji_pack(refs, m, with_n=with_n, stream=stream)
     acc, cnt, _ = shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
+                                E_per_pair=E_per_pair, stream=stream)
+    return accept_to_bool(acc, n), cnt[:n]
+
+
+def magnet_pairs(reads, refs, E: int, *, with_n: bool | None = None, E_per_pair=None,
+                 stream=None):
+    """Pack (n, m) uint8 CUDA tensors of reads and references and run MAGNET.
+
+    Returns ``(accept_bool[n], count_uint8[n])`` like ``filter_pairs``.
+    """
+    n, m = reads.shape
+    assert refs.shape == reads.shape
+    if with_n is None:
+        with_n = bool(((reads == 78).any() | (refs == 78).any()).item())
+    pr, nr = shouji_pack(reads, m, with_n=with_n, stream=stream)
+    pt, nt = shouji_pack(refs, m, with_n=with_n, stream=stream)
+    acc, cnt, _ = shouji_magnet(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
                                 E_per_pair=E_per_pair, stream=stream)
     return accept_to_bool(acc, n), cnt[:n]
 

@@ -197,3 +197,16 @@ def test_magnet_random_configurations():
         acc_o, cnt_o = oracle.shouji_batch(r_o, t_o, E, E_per_pair=e_o, threads=8, magnet=True)
         bad = np.flatnonzero((cnt != cnt_o) | (bits != acc_o))
         assert bad.size == 0, (trial, m, E, n, with_n, ep is not None, bad[:5])
+
+
+def test_magnet_pairs_convenience():
+    """magnet_pairs (pack + MAGNET in one call) on ASCII tensors, with 'N'."""
+    dev = _dev()
+    n, m, E = 1500, 120, 6
+    reads, refs = synth.pairs(n, m, seed=77, near=(0, 6), far=(7, 30), far_fraction=0.5,
+                              n_rate=0.01)
+    acc, cnt = sj.magnet_pairs(torch.from_numpy(reads).to(dev), torch.from_numpy(refs).to(dev), E)
+    torch.cuda.synchronize()
+    acc_o, cnt_o = oracle.shouji_batch(reads, refs, E, threads=8, magnet=True)
+    assert (acc.cpu().numpy() == acc_o).all()
+    assert (cnt.cpu().numpy() == cnt_o).all()
