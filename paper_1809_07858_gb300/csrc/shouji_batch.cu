@@ -217,7 +217,10 @@ __global__ void scatter_kernel(const Args *__restrict__ a, const Tables *__restr
 }
 
 // ---------------------------------------------------------------- pack
-// blockIdx.y = 0: reads, 1: refs.  A block packs 256 slots of one m-class.
+// blockIdx.y = 0: reads, 1: refs.  A block packs 128 slots (4 lanes of a
+// tile) of one m-class; the CTAs walk the blocks blockIdx.x, +gridDim.x, ...
+// This byte-gather form serves rows that are not on 16-byte boundaries and
+// exits at once otherwise (pack_async_kernel packs those).
 template <bool WITH_N>
 __global__ void __launch_bounds__(kPackThreads)
 pack_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int max_m,
