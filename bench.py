@@ -436,9 +436,12 @@ def run_ours(args, world, rank, local):
     for _ in range(2):
         pipe.run(h_reads, h_refs, n, E, h_acc, count=h_cnt, idx=h_idx)
     barrier()
+    e2e_steps_ms = []
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
+        t1 = time.perf_counter()
         e2e_acc = pipe.run(h_reads, h_refs, n, E, h_acc, count=h_cnt, idx=h_idx)
+        e2e_steps_ms.append(round(1000 * (time.perf_counter() - t1), 2))
     e2e_s = time.perf_counter() - t0
     if world > 1:
         import torch.distributed as dist
@@ -499,7 +502,7 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": dict(workload_config(n), parallelism="independent shards" if world > 1 else "1 GPU"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "step_ms": e2e_steps_ms,
                 "path": "shouji_pipeline_run, pinned host buffers, chunks of %d pairs" % args.chunk},
         "gpu_launches": 6 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "lane-ops/s",
