@@ -21,3 +21,27 @@ def cuda_device():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch.device("cuda:0")
+
+
+class HostBuffers:
+    """Two host byte buffers shared by the full-size tests of a session, grown
+    (never shrunk) to the largest request.  The inputs of every full-size test
+    are generated into them: allocating and freeing tens of GB per test leaves
+    the host reclaiming memory, which stalls host-device copies for a while
+    afterwards."""
+
+    def __init__(self):
+        self.a = self.b = None
+
+    def views(self, n, stride):
+        import numpy as np
+        need = n * stride
+        if self.a is None or self.a.size < need:
+            self.a = self.b = None
+            self.a, self.b = np.empty(need, np.uint8), np.empty(need, np.uint8)
+        return self.a[:need].reshape(n, stride), self.b[:need].reshape(n, stride)
+
+
+@pytest.fixture(scope="session")
+def host_buffers():
+    return HostBuffers()

@@ -138,7 +138,7 @@ def test_unaligned_stride_byte_path():
 
 
 @pytest.mark.slow
-def test_full_size_batch_sampled():
+def test_full_size_batch_sampled(host_buffers):
     """The benchmark's batched workload at its full size (50M pairs, lengths
     40% 100 / 40% 150 / 20% 250, E uniform in 2..12, unsorted, stride 256) in one
     graph launch: properties over every pair, and a seeded sample of 300k pairs
@@ -147,7 +147,7 @@ def test_full_size_batch_sampled():
     n = 50_000_000
     lens, Es = synth.mixed_shape(n, seed=4242)
     reads, refs = synth.pairs(n, 250, seed=4242, near=(0, 6), far=(7, 40), far_fraction=0.5,
-                              lengths=lens, stride=256)
+                              lengths=lens, stride=256, out=host_buffers.views(n, 256))
     b = sj.Batch(n, 250, 2, 12)
     acc, cnt = b.run(torch.from_numpy(reads).to(d), torch.from_numpy(refs).to(d),
                      torch.from_numpy(lens.astype(np.int16)).to(d), torch.from_numpy(Es).to(d))

@@ -137,13 +137,13 @@ def test_magnet_count_modes_with_short_reads():
             assert b[i] == (co <= E)
 
 
-def test_magnet_full_size():
+def test_magnet_full_size(host_buffers):
     """The benchmark's MAGNET workload (30M pairs, m = 100, E = 5, half of them
     near, half far) in one launch, every pair checked against the oracle (run
     on all host cores)."""
     dev = _dev()
     n, m, E = 30_000_000, 100, 5
-    reads, refs = synth.workload("sweep", n, E=E)
+    reads, refs = synth.workload("sweep", n, E=E, out=host_buffers.views(n, m))
     pr, _ = sj.shouji_pack(torch.from_numpy(reads).to(dev), m)
     pt, _ = sj.shouji_pack(torch.from_numpy(refs).to(dev), m)
     acc, cnt, _ = sj.shouji_magnet(pr, pt, m, n, E)

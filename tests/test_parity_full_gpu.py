@@ -55,12 +55,14 @@ def check(reads, refs, m, E, with_n):
 
 
 @pytest.mark.parametrize("E", [0, 5, 10])
-def test_sweep_30M(E):
-    reads, refs = synth.workload("sweep", 30_000_000, E=E)
+def test_sweep_30M(E, host_buffers):
+    reads, refs = synth.workload("sweep", 30_000_000, E=E,
+                                 out=host_buffers.views(30_000_000, 100))
     check(reads, refs, 100, E, False)
 
 
 @pytest.mark.parametrize("m,E", [(150, 15), (250, 15)])
-def test_long_10M_with_N(m, E):
-    reads, refs = synth.workload("long", 10_000_000, m=m, E=E)
+def test_long_10M_with_N(m, E, host_buffers):
+    reads, refs = synth.workload("long", 10_000_000, m=m, E=E,
+                                 out=host_buffers.views(10_000_000, m))
     check(reads, refs, m, E, True)
