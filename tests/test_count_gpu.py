@@ -38,3 +38,28 @@ def test_count_modes_bit_exact(m, E):
             _, c = oracle.shouji_mode(reads[i, :mp[i]].tobytes(), refs[i].tobytes(), E, mode)
             assert cnt[i] == c, (mode, i, cnt[i], c)
             assert bits[i] == (c <= E)
+
+
+def test_count_modes_per_pair_thresholds():
+    """shouji_count with per-pair thresholds (values above E act as E)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    m, E, n = 100, 8, 3000
+    reads, refs = synth.pairs(n, m, seed=808, near=(0, E), far=(E + 1, 30), far_fraction=0.5)
+    ep = np.random.default_rng(9).integers(0, E + 3, size=n).astype(np.uint8)
+    pr, _ = sj.shouji_pack(torch.from_numpy(reads).to(dev), m)
+    pt, _ = sj.shouji_pack(torch.from_numpy(refs).to(dev), m)
+    ep_d = torch.from_numpy(ep).to(dev)
+    _, _, vec = sj.shouji_filter(pr, pt, m, n, E, E_per_pair=ep_d, vectors=True)
+    for mode in range(4):
+        acc, cnt = sj.shouji_count(vec, m, n, E, mode, E_per_pair=ep_d)
+        torch.cuda.synchronize()
+        cnt = cnt[:n].cpu().numpy()
+        w = acc.cpu().numpy().view(np.uint32)
+        bits = ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1)[:n].astype(bool)
+        for i in range(0, n, 7):
+            e = min(int(ep[i]), E)
+            _, c = oracle.shouji_mode(reads[i].tobytes(), refs[i].tobytes(), e, mode)
+            assert cnt[i] == c, (mode, i)
+            assert bits[i] == (c <= e), (mode, i)

@@ -137,6 +137,24 @@ def test_pack_layout(m, pad):
     assert (full[n:] == 0).all()
 
 
+@pytest.mark.parametrize("m,off", [(100, 4), (100, 1), (33, 0), (33, 3), (250, 8)])
+def test_pack_rows_at_unaligned_base(m, off):
+    """Contiguous rows (stride == m) whose first byte is not on a 16-byte
+    boundary: the 4-byte and the per-row copy forms of the pack."""
+    rng = np.random.default_rng(m + off)
+    n = 3000
+    seqs = rng.choice(np.frombuffer(b"ACGTN", np.uint8), size=(n, m))
+    buf = torch.zeros(n * m + 64, dtype=torch.uint8, device=dev())
+    view = buf[off: off + n * m]
+    view.copy_(torch.from_numpy(seqs.reshape(-1)).to(dev()))
+    packed, nmask = sj.shouji_pack(view, m, n=n, stride=m, with_n=True)
+    torch.cuda.synchronize()
+    codes = unpack_planes(packed.cpu().numpy(), n, m)
+    want = np.vectorize(CODE.get)(seqs).astype(np.uint8)
+    assert (codes == want).all()
+    assert (unpack_sliced(nmask.cpu().numpy(), n, m) == (seqs == ord("N"))).all()
+
+
 def test_pack_without_mask_reads_N_as_G():
     seqs = np.frombuffer(b"ACGTN" * 20, np.uint8).reshape(1, 100).repeat(40, 0)
     packed, nm = sj.shouji_pack(to_dev(seqs), 100)
