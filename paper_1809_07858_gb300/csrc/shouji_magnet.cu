@@ -44,6 +44,8 @@
 namespace shouji {
 namespace {
 
+// Two warps per CTA: a CTA holds its registers until its slowest warp is
+// done, and smaller CTAs let an SM take new groups sooner.
 constexpr int kMagnetThreads = 64;
 constexpr int kMaxStack = SHOUJI_MAX_E + 3;  // 1 + one net push per extraction
 constexpr int kMainRank = 2 * SHOUJI_MAX_E;  // after every upper_j and lower_j
