@@ -81,6 +81,20 @@ size_t shouji_packed_words(size_t n, uint32_t m);
 size_t shouji_nmask_words(size_t n, uint32_t m);
 
 /*
+ * shouji_wait_failures -- how many bounded device waits ran out.
+ *
+ * Synchronizes the device, writes to *count the number of staging waits of
+ * shouji_pack (one per CTA that gave up) that ran out since the last call,
+ * and resets that number.  Nonzero means that the output of some pack launch
+ * is incomplete.  No wait runs out in normal operation: the count exists so
+ * that a copy that never lands ends the kernel instead of hanging it.
+ *   count   host, written.
+ * Errors: SHOUJI_EINVAL for NULL count; SHOUJI_ECUDA when the synchronize or
+ * the read fails (e.g. an earlier asynchronous error).
+ */
+shouji_status shouji_wait_failures(uint32_t *count);
+
+/*
  * shouji_pack -- ASCII sequences to the packed bit-sliced layout.
  *
  * The FPGA design of the paper compares bases with XOR on an encoded form of
@@ -96,6 +110,10 @@ size_t shouji_nmask_words(size_t n, uint32_t m);
  *           as 'G' (no mask).
  * Errors: SHOUJI_EINVAL for NULL seqs/packed (with n > 0), m out of range,
  * stride < m; SHOUJI_ECUDA on a launch failure.
+ * Contiguous rows on a 16-byte boundary (stride == m, seqs % 16 == 0) are
+ * staged by bulk copies whose completion the kernel waits for with a limit of
+ * about one second; a wait that runs out leaves part of `packed` unwritten
+ * and is counted for shouji_wait_failures().
  */
 shouji_status shouji_pack(const uint8_t *seqs, uint64_t stride, size_t n,
                           uint32_t m, uint32_t *packed, uint32_t *nmask,

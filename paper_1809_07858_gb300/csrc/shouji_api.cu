@@ -73,6 +73,13 @@ shouji_status shouji_pack(const uint8_t *seqs, uint64_t stride, size_t n, uint32
     return cuda_status(launch_pack(seqs, stride, n, (int)m, packed, nmask, (cudaStream_t)stream));
 }
 
+shouji_status shouji_wait_failures(uint32_t *count)
+{
+    if (!count)
+        return SHOUJI_EINVAL;
+    return cuda_status(take_wait_failures(count));
+}
+
 shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
                             const uint32_t *reads_nmask, const uint32_t *refs_nmask,
                             uint32_t m, size_t n_pairs, int E, const uint8_t *E_per_pair,

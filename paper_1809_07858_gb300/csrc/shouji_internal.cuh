@@ -22,6 +22,9 @@ shouji_status cuda_status(cudaError_t e);
 // Launchers (argument checks are done by the C-ABI layer).
 cudaError_t launch_pack(const uint8_t *seqs, uint64_t stride, size_t n, int m,
                         uint32_t *packed, uint32_t *nmask, cudaStream_t s);
+// Synchronizes the device, then reads and resets the count of pack staging
+// waits that ran out.
+cudaError_t take_wait_failures(uint32_t *count);
 
 struct FilterArgs {
     const uint2 *reads, *refs;               // packed pairs (hi, lo) words

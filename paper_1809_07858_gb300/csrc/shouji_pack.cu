@@ -8,12 +8,12 @@
 //
 // One CTA of 256 threads packs 256 sequences = 8 lanes of a 1024-sequence
 // tile (for contiguous rows on a 16-byte boundary, a persistent CTA walks
-// such blocks with double buffering; see pack_stream_kernel).  Phase 1
-// copies the CTA's rows into shared memory as one dense block
-// (row r at byte r*m).  When the rows are contiguous in global memory
-// (stride == m) the block is a single contiguous range and is copied with
-// 16-byte (or 4-byte) loads, four in flight per thread; otherwise row by
-// row.  Phase 2: a thread owns (lane, 4 consecutive positions); it reads one
+// such blocks with double buffering and bulk copies; see
+// pack_stream_kernel).  Phase 1 copies the CTA's rows into shared memory as
+// one dense block (row r at byte r*m).  When the rows are contiguous in
+// global memory (stride == m) the block is a single contiguous range and is
+// copied with 16-byte (or 4-byte) loads, four in flight per thread;
+// otherwise row by row.  Phase 2: a thread owns (lane, 4 consecutive positions); it reads one
 // word (4 bases) of each of the lane's 32 sequences, gathers bit 2 / bit 1 /
 // is-'N' of every byte into byte-sliced words with shifts and masks, and a
 // 4x4 byte transpose (PRMT) turns them into the four output words of each
@@ -102,65 +102,90 @@ pack_kernel(const uint8_t *__restrict__ seqs, uint64_t stride, size_t n, int m,
     pack_transpose<WITH_N, ALIGNED>(sm, m, m, tile, lane0, packed, nmask, rot_step, kPackThreads);
 }
 
+// Bounded waits of pack_stream_kernel that ran out (see shouji_wait_failures).
+__device__ unsigned int g_pack_wait_failures;
+
 // Contiguous rows on a 16-byte boundary (the common case): a persistent,
 // double-buffered form.  Each CTA walks blocks blockIdx.x, +gridDim.x, ...;
-// while it transposes block i from one buffer, the 16-byte chunks of block
-// i+1 are already on their way into the other with cp.async, so the loads of
-// the next block overlap the transposition of this one.  A chunk past the
-// CTA's rows is zero-filled by the copy itself (source size 0); the last
-// partial chunk copies only its valid bytes.
+// while it transposes block i from one buffer, one bulk copy (the TMA unit)
+// brings the rows of block i+1 into the other, completing on that buffer's
+// mbarrier, so the loads of the next block overlap the transposition of this
+// one.  The copy moves the block's bytes rounded down to 16; the threads add
+// the last few bytes of a partial block and the zero padding after the rows.
+// A wait that runs out (a copy that never lands) ends the CTA and counts one
+// failure; the CTA first waits, bounded too, for its other copy in flight.
 template <bool WITH_N, bool ALIGNED>
 __global__ void __launch_bounds__(kPackThreads)
 pack_stream_kernel(const uint8_t *__restrict__ seqs, size_t n, int m,
                    uint32_t *__restrict__ packed, uint32_t *__restrict__ nmask, int rot_step,
                    size_t n_blocks, int buf_bytes)
 {
-    extern __shared__ __align__(16) uint32_t sm[];
+    extern __shared__ __align__(128) uint32_t sm[];
+    __shared__ __align__(8) uint64_t full[2];
     uint8_t *bufs = reinterpret_cast<uint8_t *>(sm);
     const int tid = threadIdx.x;
-    const int chunks = buf_bytes >> 4;
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
 
-    auto issue = [&](size_t blk, uint8_t *dst) {
+    // staged bytes holding real rows; blocks of the last tile may start at or
+    // past n and stage none
+    auto row_bytes = [&](size_t blk) -> int {
         const size_t seq0 = blk * kPackSeqs;
-        // blocks of the last tile may start at or past n: they stage no rows
         const size_t left = seq0 < n ? n - seq0 : 0;
-        const int rows = (int)(left < (size_t)kPackSeqs ? left : (size_t)kPackSeqs);
-        const int nbytes = rows * m;
-        const uint8_t *src = seqs + seq0 * (size_t)m;
-        for (int k = tid; k < chunks; k += kPackThreads) {
-            const int rem = nbytes - 16 * k;
-            const uint32_t bytes = rem >= 16 ? 16u : rem > 0 ? (uint32_t)rem : 0u;
-            cp_async16(dst + 16 * k, bytes ? src + 16 * k : seqs, bytes);
-        }
+        return (int)(left < (size_t)kPackSeqs ? left : (size_t)kPackSeqs) * m;
+    };
+    auto issue = [&](size_t blk, int b) {  // one thread
+        const uint32_t bytes = (uint32_t)row_bytes(blk) & ~15u;
+        mbar_arrive_expect_tx(&full[b], bytes);
+        if (bytes)
+            bulk_copy_g2s(bufs + (size_t)b * buf_bytes, seqs + blk * kPackSeqs * (size_t)m, bytes,
+                          &full[b]);
     };
 
     size_t blk = blockIdx.x;
-    if (blk < n_blocks)
-        issue(blk, bufs);
-    cp_async_commit();
+    if (tid == 0 && blk < n_blocks)
+        issue(blk, 0);
+    uint32_t parity = 0;  // bit b: parity of the phase of full[b] to wait for
     for (int i = 0; blk < n_blocks; ++i, blk += gridDim.x) {
+        const int b = i & 1;
         const size_t next = blk + gridDim.x;
-        if (next < n_blocks)
-            issue(next, bufs + (size_t)((i + 1) & 1) * buf_bytes);
-        cp_async_commit();  // possibly empty: keeps one group per block
-        cp_async_wait<1>();  // this thread's copies of block blk are in
-        __syncthreads();    // and everyone's
+        if (tid == 0 && next < n_blocks) {
+            fence_proxy_async_smem();  // buffer b^1 was read in the last round
+            issue(next, b ^ 1);
+        }
+        const bool ok = mbar_wait_bounded(&full[b], (parity >> b) & 1u);
+        parity ^= 1u << b;
+        uint8_t *buf = bufs + (size_t)b * buf_bytes;
+        const int nbytes = row_bytes(blk);
         const size_t seq0 = blk * kPackSeqs;
-        pack_transpose<WITH_N, ALIGNED>(
-            reinterpret_cast<const uint32_t *>(bufs + (size_t)(i & 1) * buf_bytes), m, m,
-            seq0 / kTile, (int)((seq0 % kTile) / 32), packed, nmask, rot_step, kPackThreads);
-        __syncthreads();    // the buffer may be refilled
+        for (int x = (nbytes & ~15) + tid; x < buf_bytes; x += kPackThreads)
+            buf[x] = x < nbytes ? __ldg(seqs + seq0 * (size_t)m + x) : (uint8_t)0;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicAdd(&g_pack_wait_failures, 1u);
+                if (next < n_blocks)
+                    mbar_wait_bounded(&full[b ^ 1], (parity >> (b ^ 1)) & 1u);
+            }
+            return;
+        }
+        pack_transpose<WITH_N, ALIGNED>(reinterpret_cast<const uint32_t *>(buf), m, m,
+                                        seq0 / kTile, (int)((seq0 % kTile) / 32), packed, nmask,
+                                        rot_step, kPackThreads);
+        __syncthreads();  // the buffer may be refilled
     }
-    cp_async_wait<0>();
 }
 
 template <bool WITH_N, bool ALIGNED>
 cudaError_t launch_stream_ta(const uint8_t *seqs, size_t n, int m, uint32_t *packed,
                              uint32_t *nmask, int rot, cudaStream_t s)
 {
-    // one buffer: 256 rows of m bytes and 16 bytes of zero padding, in
-    // whole 16-byte chunks
-    const int buf_bytes = (kPackSeqs * m + 16 + 15) / 16 * 16;
+    // one buffer: 256 rows of m bytes and 16 bytes of zero padding, rounded
+    // up to 128 bytes
+    const int buf_bytes = (kPackSeqs * m + 16 + 127) / 128 * 128;
     const size_t smem = 2 * (size_t)buf_bytes;
     const size_t n_blocks = tiles_of(n) * (kTile / kPackSeqs);
     cudaError_t e = cudaFuncSetAttribute(pack_stream_kernel<WITH_N, ALIGNED>,
@@ -234,6 +259,20 @@ cudaError_t launch_pack(const uint8_t *seqs, uint64_t stride, size_t n, int m,
     if (nmask)
         return launch_pack_t<true>(seqs, stride, n, m, packed, nmask, s);
     return launch_pack_t<false>(seqs, stride, n, m, packed, nmask, s);
+}
+
+cudaError_t take_wait_failures(uint32_t *count)
+{
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned int v = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyFromSymbol(&v, g_pack_wait_failures, sizeof v);
+    if (e == cudaSuccess && v) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_pack_wait_failures, &zero, sizeof zero);
+    }
+    *count = v;
+    return e;
 }
 
 }  // namespace shouji

@@ -155,6 +155,28 @@ def test_pack_rows_at_unaligned_base(m, off):
     assert (unpack_sliced(nmask.cpu().numpy(), n, m) == (seqs == ord("N"))).all()
 
 
+@pytest.mark.parametrize("m,n", [(33, 1_000_003), (100, 400_001), (255, 150_001), (64, 262_144)])
+def test_pack_stream_many_blocks_per_cta(m, n):
+    """Contiguous rows on a 16-byte boundary: the persistent pack that stages
+    blocks with bulk copies, at sizes where each CTA walks several blocks and
+    the last block is partial (or, for 262,144, exactly full); no staging
+    wait may run out."""
+    rng = np.random.default_rng(m * 1000 + n % 1000)
+    seqs = rng.choice(np.frombuffer(b"ACGTN", np.uint8), size=(n, m), p=[0.24, 0.24, 0.24, 0.24, 0.04])
+    d = to_dev(seqs)
+    assert d.data_ptr() % 16 == 0
+    packed, nmask = sj.shouji_pack(d, m, with_n=True)
+    assert sj.shouji_wait_failures() == 0
+    codes = unpack_planes(packed.cpu().numpy(), n, m)
+    lut = np.zeros(256, np.uint8)
+    for k, v in CODE.items():
+        lut[k] = v
+    assert (codes == lut[seqs]).all()
+    assert (unpack_sliced(nmask.cpu().numpy(), n, m) == (seqs == ord("N"))).all()
+    tiles = (n + 1023) // 1024
+    assert (unpack_planes(packed.cpu().numpy(), tiles * 1024, m)[n:] == 0).all()
+
+
 def test_pack_without_mask_reads_N_as_G():
     seqs = np.frombuffer(b"ACGTN" * 20, np.uint8).reshape(1, 100).repeat(40, 0)
     packed, nm = sj.shouji_pack(to_dev(seqs), 100)
