@@ -95,6 +95,20 @@ size_t shouji_nmask_words(size_t n, uint32_t m);
 shouji_status shouji_wait_failures(uint32_t *count);
 
 /*
+ * shouji_selftest_pack_wait -- exercises the path above without a fault.
+ *
+ * Packs 1024 sequences of 4 bases (one tile: 4 blocks of 256 rows, one CTA
+ * each) with every staging copy announced to its mbarrier as 16 bytes longer
+ * than it is, so that no wait can complete: each CTA's wait runs out after
+ * about a second.  Synchronizes the device and writes to *failures the
+ * failures counted by that launch (4); failures counted before the call are
+ * discarded.  Takes about a second; the device stays usable.
+ *   failures  host, written.
+ * Errors: SHOUJI_EINVAL for NULL failures; SHOUJI_ECUDA on a CUDA failure.
+ */
+shouji_status shouji_selftest_pack_wait(uint32_t *failures);
+
+/*
  * shouji_pack -- ASCII sequences to the packed bit-sliced layout.
  *
  * The FPGA design of the paper compares bases with XOR on an encoded form of

@@ -22,6 +22,7 @@ SHOUJI_NOALLOC_MAX_PAIRS = 1 << 29
 __all__ = [
     "ShoujiError", "SHOUJI_TILE", "SHOUJI_MAX_M", "SHOUJI_MAX_E", "LIB_PATH",
     "load_library", "shouji_status_string", "shouji_last_cuda_error", "shouji_wait_failures",
+    "shouji_selftest_pack_wait",
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
@@ -58,6 +59,8 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_last_cuda_error.restype = ctypes.c_int
     lib.shouji_wait_failures.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
     lib.shouji_wait_failures.restype = ctypes.c_int
+    lib.shouji_selftest_pack_wait.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+    lib.shouji_selftest_pack_wait.restype = ctypes.c_int
     lib.shouji_packed_words.argtypes = [sz, u32]
     lib.shouji_packed_words.restype = sz
     lib.shouji_nmask_words.argtypes = [sz, u32]
@@ -124,6 +127,14 @@ def shouji_wait_failures() -> int:
     staging waits that ran out (0 in normal operation)."""
     c = ctypes.c_uint32(0)
     _check(load_library().shouji_wait_failures(ctypes.byref(c)), "shouji_wait_failures")
+    return c.value
+
+
+def shouji_selftest_pack_wait() -> int:
+    """Run the pack with every staging wait made to run out (about a second);
+    return the failures counted (4)."""
+    c = ctypes.c_uint32(0)
+    _check(load_library().shouji_selftest_pack_wait(ctypes.byref(c)), "shouji_selftest_pack_wait")
     return c.value
 
 

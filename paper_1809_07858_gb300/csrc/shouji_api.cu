@@ -80,6 +80,13 @@ shouji_status shouji_wait_failures(uint32_t *count)
     return cuda_status(take_wait_failures(count));
 }
 
+shouji_status shouji_selftest_pack_wait(uint32_t *failures)
+{
+    if (!failures)
+        return SHOUJI_EINVAL;
+    return cuda_status(selftest_pack_wait(failures));
+}
+
 shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
                             const uint32_t *reads_nmask, const uint32_t *refs_nmask,
                             uint32_t m, size_t n_pairs, int E, const uint8_t *E_per_pair,

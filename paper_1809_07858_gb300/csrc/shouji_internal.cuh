@@ -25,6 +25,9 @@ cudaError_t launch_pack(const uint8_t *seqs, uint64_t stride, size_t n, int m,
 // Synchronizes the device, then reads and resets the count of pack staging
 // waits that ran out.
 cudaError_t take_wait_failures(uint32_t *count);
+// Runs the pack on 1024 sequences with every staging wait made to run out;
+// writes the failures counted.
+cudaError_t selftest_pack_wait(uint32_t *failures);
 
 struct FilterArgs {
     const uint2 *reads, *refs;               // packed pairs (hi, lo) words

@@ -114,11 +114,13 @@ __device__ unsigned int g_pack_wait_failures;
 // the last few bytes of a partial block and the zero padding after the rows.
 // A wait that runs out (a copy that never lands) ends the CTA and counts one
 // failure; the CTA first waits, bounded too, for its other copy in flight.
+// extra_tx is 0 except in the self-test of that path, which announces each
+// copy 16 bytes longer than it is so that no wait can complete.
 template <bool WITH_N, bool ALIGNED>
 __global__ void __launch_bounds__(kPackThreads)
 pack_stream_kernel(const uint8_t *__restrict__ seqs, size_t n, int m,
                    uint32_t *__restrict__ packed, uint32_t *__restrict__ nmask, int rot_step,
-                   size_t n_blocks, int buf_bytes)
+                   size_t n_blocks, int buf_bytes, uint32_t extra_tx)
 {
     extern __shared__ __align__(128) uint32_t sm[];
     __shared__ __align__(8) uint64_t full[2];
@@ -140,7 +142,7 @@ pack_stream_kernel(const uint8_t *__restrict__ seqs, size_t n, int m,
     };
     auto issue = [&](size_t blk, int b) {  // one thread
         const uint32_t bytes = (uint32_t)row_bytes(blk) & ~15u;
-        mbar_arrive_expect_tx(&full[b], bytes);
+        mbar_arrive_expect_tx(&full[b], bytes + extra_tx);
         if (bytes)
             bulk_copy_g2s(bufs + (size_t)b * buf_bytes, seqs + blk * kPackSeqs * (size_t)m, bytes,
                           &full[b]);
@@ -181,7 +183,7 @@ pack_stream_kernel(const uint8_t *__restrict__ seqs, size_t n, int m,
 
 template <bool WITH_N, bool ALIGNED>
 cudaError_t launch_stream_ta(const uint8_t *seqs, size_t n, int m, uint32_t *packed,
-                             uint32_t *nmask, int rot, cudaStream_t s)
+                             uint32_t *nmask, int rot, cudaStream_t s, uint32_t extra_tx = 0)
 {
     // one buffer: 256 rows of m bytes and 16 bytes of zero padding, rounded
     // up to 128 bytes
@@ -203,7 +205,7 @@ cudaError_t launch_stream_ta(const uint8_t *seqs, size_t n, int m, uint32_t *pac
     const size_t full = (size_t)sms * (per_sm > 0 ? per_sm : 1);
     const unsigned grid = (unsigned)(n_blocks < full ? n_blocks : full);
     pack_stream_kernel<WITH_N, ALIGNED><<<grid, kPackThreads, smem, s>>>(
-        seqs, n, m, packed, nmask, rot, n_blocks, buf_bytes);
+        seqs, n, m, packed, nmask, rot, n_blocks, buf_bytes, extra_tx);
     return cudaGetLastError();
 }
 
@@ -272,6 +274,30 @@ cudaError_t take_wait_failures(uint32_t *count)
         e = cudaMemcpyToSymbol(g_pack_wait_failures, &zero, sizeof zero);
     }
     *count = v;
+    return e;
+}
+
+cudaError_t selftest_pack_wait(uint32_t *failures)
+{
+    // 1024 sequences of 4 bases: one tile, 4 blocks, one per CTA
+    constexpr size_t n = 1024;
+    constexpr int m = 4;
+    *failures = 0;
+    uint32_t before = 0;
+    cudaError_t e = take_wait_failures(&before);
+    if (e != cudaSuccess)
+        return e;
+    uint8_t *seqs = nullptr;
+    uint32_t *packed = nullptr;
+    if ((e = cudaMalloc(&seqs, n * m)) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&packed, tiles_of(n) * m * 64 * sizeof(uint32_t))) == cudaSuccess &&
+        (e = cudaMemset(seqs, 'A', n * m)) == cudaSuccess &&
+        (e = launch_stream_ta<false, true>(seqs, n, m, packed, nullptr, rotation_step(m), 0,
+                                           16u)) == cudaSuccess)
+        e = take_wait_failures(failures);
+    cudaFree(packed);
+    cudaFree(seqs);
     return e;
 }
 

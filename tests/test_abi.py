@@ -78,6 +78,7 @@ def test_host_argument_checks_return_einval():
                              None, None, None) == EINVAL
     assert lib.shouji_magnet(None, None, None, None, 100, 0, 5, None, None, None, None, None) == OK
     assert lib.shouji_wait_failures(None) == EINVAL
+    assert lib.shouji_selftest_pack_wait(None) == EINVAL
     # compact: short or misaligned workspace, too many pairs, nulls
     assert lib.shouji_compact(fake, 1000, fake, fake, fake, 0, None) == EINVAL
     assert lib.shouji_compact(fake, 1000, fake, fake, ctypes.c_void_p(0x1008), 1 << 20, None) == EINVAL

@@ -177,6 +177,26 @@ def test_pack_stream_many_blocks_per_cta(m, n):
     assert (unpack_planes(packed.cpu().numpy(), tiles * 1024, m)[n:] == 0).all()
 
 
+def test_pack_wait_gives_up_and_counts():
+    """The pack's bounded staging wait: with every copy announced 16 bytes
+    longer than it is, each of the self-test's 4 CTAs gives up after about a
+    second and counts one failure; the device stays usable, and a normal pack
+    afterwards is exact and counts none."""
+    import time
+    assert sj.shouji_wait_failures() == 0
+    t0 = time.time()
+    assert sj.shouji_selftest_pack_wait() == 4
+    assert time.time() - t0 < 60
+    rng = np.random.default_rng(5)
+    seqs = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=(5000, 100))
+    packed, _ = sj.shouji_pack(to_dev(seqs), 100)
+    assert sj.shouji_wait_failures() == 0
+    lut = np.zeros(256, np.uint8)
+    for k, v in CODE.items():
+        lut[k] = v
+    assert (unpack_planes(packed.cpu().numpy(), 5000, 100) == lut[seqs]).all()
+
+
 def test_pack_without_mask_reads_N_as_G():
     seqs = np.frombuffer(b"ACGTN" * 20, np.uint8).reshape(1, 100).repeat(40, 0)
     packed, nm = sj.shouji_pack(to_dev(seqs), 100)
