@@ -4,8 +4,8 @@ Workload (synthetic, shaped like the paper's m=100 datasets): 30,000,000 pairs
 of length m = 100 at threshold E = 5, half near (k ~ U{0..5} edits) and half
 far (k ~ U{6..25}), ASCII reads and references resident in HBM (6 GB, larger
 than L2, so no flush is needed between steps).  One step is the whole hot path
-over the batch: shouji_pack (reads), shouji_pack (refs), shouji_filter,
-shouji_compact.  ``e2e`` runs the same batch through the host pipeline
+over the batch: shouji_pack_filter (both packs and the filter in one
+warp-specialized kernel), then shouji_compact.  ``e2e`` runs the same batch through the host pipeline
 (shouji_pipeline_run: pinned host buffers in, accept bits, counts and survivor
 indices out), with every copy inside the timed region.
 
@@ -41,6 +41,16 @@ ALU_LANES_PER_SM_CLK = 64   # LOP3/SHF/PRMT issue rate of the integer ALU pipe p
 # taken on; scaled to a 30M-pair launch.  Reported as null once the kernel
 # source changes.
 FILTER_TRAFFIC = {"0325f129af588db8": 1.540e9}  # profiles/filter_kernel_E5_m100.md
+# The same for the fused pack + filter kernel, keyed by the hash of its sources.
+FUSED_TRAFFIC = {"79629851786b73f0": 8.845e9}  # profiles/pack_filter_kernel_m100_E5.md
+FUSED_SOURCES = ("shouji_pack_filter.cu", "shouji_pack.cuh", "shouji_filter.cuh")
+
+
+def fused_bytes_per_pair(m: int) -> float:
+    """Algorithmic DRAM bytes per pair of the fused pack + filter: both ASCII
+    rows in (2m), both packed rows out (2 x m/4), an accept bit and a count
+    byte out."""
+    return 2 * m + 2 * (m / 4) + 1 / 8 + 1
 
 
 def alu_ops_per_pair(m: int, E: int) -> float:
@@ -54,12 +64,16 @@ def alu_ops_per_pair(m: int, E: int) -> float:
     return m * per_window / 32.0
 
 
-def filter_source_hash() -> str:
+def source_hash(names=("shouji_filter.cuh",)) -> str:
     h = hashlib.sha256()
-    for name in ("shouji_filter.cuh",):
+    for name in names:
         with open(os.path.join(ROOT, "paper_1809_07858_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def filter_source_hash() -> str:
+    return source_hash()
 
 
 def measured_peaks():
@@ -374,7 +388,7 @@ def run_ours(args, world, rank, local):
     ws = torch.empty(max(16, sj.shouji_compact_workspace_size(n)), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    ev = {k: [] for k in ("pack0", "pack1", "filter0", "filter1", "compact0", "compact1")}
+    ev = {k: [] for k in ("fused0", "fused1", "compact0", "compact1")}
 
     def step(timed):
         def mark(k):
@@ -382,14 +396,11 @@ def run_ours(args, world, rank, local):
                 e = torch.cuda.Event(enable_timing=True)
                 e.record(stream)
                 ev[k].append(e)
-        mark("pack0")
-        sj.shouji_pack(d_reads, M, packed=packed_r, stream=stream)
-        sj.shouji_pack(d_refs, M, packed=packed_t, stream=stream)
-        mark("pack1")
-        mark("filter0")
-        sj.shouji_filter(packed_r, packed_t, M, n, E, out_accept=accept, out_count=count,
-                         stream=stream)
-        mark("filter1")
+        mark("fused0")
+        sj.shouji_pack_filter(d_reads, d_refs, M, E, packed_reads=packed_r,
+                              packed_refs=packed_t, out_accept=accept, out_count=count,
+                              stream=stream)
+        mark("fused1")
         mark("compact0")
         sj.shouji_compact(accept, n, out_idx=idx, out_n=n_acc, workspace=ws, stream=stream)
         mark("compact1")
@@ -424,8 +435,30 @@ def run_ours(args, world, rank, local):
     def avg(a, b):
         return sum(x.elapsed_time(y) for x, y in zip(ev[a], ev[b])) / max(1, len(ev[a]))
 
-    pack_ms, filter_ms, compact_ms = avg("pack0", "pack1"), avg("filter0", "filter1"), avg("compact0", "compact1")
+    fused_ms, compact_ms = avg("fused0", "fused1"), avg("compact0", "compact1")
     n_accepted = int(n_acc.item())
+
+    # For comparison, outside the timed region: the same pack and filter as
+    # separate launches (shouji_pack twice, then shouji_filter).
+    sep = {k: [] for k in ("p0", "p1", "f1")}
+    for r in range(13):
+        for k in ("p0", "p1", "f1"):
+            e = torch.cuda.Event(enable_timing=True)
+            if k == "p0":
+                e.record(stream)
+                sj.shouji_pack(d_reads, M, packed=packed_r, stream=stream)
+                sj.shouji_pack(d_refs, M, packed=packed_t, stream=stream)
+            elif k == "p1":
+                e.record(stream)
+                sj.shouji_filter(packed_r, packed_t, M, n, E, out_accept=accept, out_count=count,
+                                 stream=stream)
+            else:
+                e.record(stream)
+            if r >= 3:
+                sep[k].append(e)
+    torch.cuda.synchronize(dev)
+    pack_ms = sum(a.elapsed_time(b) for a, b in zip(sep["p0"], sep["p1"])) / len(sep["p0"])
+    filter_ms = sum(a.elapsed_time(b) for a, b in zip(sep["p1"], sep["f1"])) / len(sep["p1"])
 
     # End to end through the host pipeline: pinned host ASCII in, accept words,
     # counts and survivor indices out, every copy inside the timed region.
@@ -464,6 +497,9 @@ def run_ours(args, world, rank, local):
     achieved = ops_launch / (filter_ms * 1e-3)
     src = filter_source_hash()
     traffic = FILTER_TRAFFIC.get(src)
+    hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
+    fused_src = source_hash(FUSED_SOURCES)
+    fused_gbs = fused_bytes_per_pair(M) * n / (fused_ms * 1e-3) / 1e9
     value = world * n * args.steps / (elapsed_ms * 1e-3)
     e2e_value = world * n * args.e2e_steps / e2e_s
     h2d = 2 * n * M
@@ -504,14 +540,22 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "step_ms": e2e_steps_ms,
                 "path": "shouji_pipeline_run, pinned host buffers, chunks of %d pairs" % args.chunk},
-        "gpu_launches": 6 * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "lane-ops/s",
-                     "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "shouji_filter", "ops_per_pair": alu_ops_per_pair(M, E),
-                     "peak_basis": "%d SMs x %d lane-ops/clk x %.0f MHz (max SM clock)" % (
-                         sms, ALU_LANES_PER_SM_CLK, sm_max),
-                     "filter_src": src},
-        "kernels_ms": {"pack_x2": pack_ms, "filter": filter_ms, "compact": compact_ms},
+        "gpu_launches": 4 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": fused_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": fused_gbs / hbm_peak, "traffic": FUSED_TRAFFIC.get(fused_src),
+                     "kernel": "shouji_pack_filter (pack_filter_kernel)",
+                     "bytes_per_pair": fused_bytes_per_pair(M),
+                     "peak_basis": "measured HBM copy bandwidth",
+                     "alu_frac": ops_launch / (fused_ms * 1e-3) / peak_ops,
+                     "alu_basis": "%.2f algorithmic filter lane-ops per pair over %d SMs x %d "
+                                  "lane-ops/clk x %.0f MHz" % (alu_ops_per_pair(M, E), sms,
+                                                               ALU_LANES_PER_SM_CLK, sm_max),
+                     "src": fused_src},
+        "kernels_ms": {"pack_filter": fused_ms, "compact": compact_ms},
+        "separate": {"pack_x2_ms": pack_ms, "filter_ms": filter_ms,
+                     "filter_roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
+                                         "unit": "lane-ops/s", "frac": achieved / peak_ops,
+                                         "traffic": traffic, "filter_src": src}},
         "accepted": n_accepted,
         "clocks": clocks,
         "cpu_baseline": cpu,

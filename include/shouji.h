@@ -83,11 +83,13 @@ size_t shouji_nmask_words(size_t n, uint32_t m);
 /*
  * shouji_wait_failures -- how many bounded device waits ran out.
  *
- * Synchronizes the device, writes to *count the number of staging waits of
- * shouji_pack (one per CTA that gave up) that ran out since the last call,
- * and resets that number.  Nonzero means that the output of some pack launch
- * is incomplete.  No wait runs out in normal operation: the count exists so
- * that a copy that never lands ends the kernel instead of hanging it.
+ * Synchronizes the device, writes to *count the number of bounded waits that
+ * ran out since the last call (staging waits of shouji_pack, one per CTA that
+ * gave up, and hand-over waits of shouji_pack_filter, one per warp group that
+ * gave up), and resets that number.  Nonzero means that the output of some
+ * launch is incomplete.  No wait runs out in normal operation: the count
+ * exists so that a copy that never lands ends the kernel instead of hanging
+ * it.
  *   count   host, written.
  * Errors: SHOUJI_EINVAL for NULL count; SHOUJI_ECUDA when the synchronize or
  * the read fails (e.g. an earlier asynchronous error).
@@ -176,6 +178,36 @@ shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
                             size_t n_pairs, int E, const uint8_t *E_per_pair,
                             uint32_t *out_accept, uint8_t *out_count,
                             uint32_t *out_vectors, void *stream);
+
+/*
+ * shouji_pack_filter -- shouji_pack of the reads and of the refs followed by
+ * shouji_filter (no N masks, one threshold), with the same outputs.
+ *
+ * When both row sets are contiguous (stride == m) on 16-byte boundaries,
+ * E <= 5 and m <= 199, this is one kernel: per SM, 16 warps stream and pack
+ * 1024-pair tiles while 8 warps filter the tiles packed before, so the
+ * HBM-bound pack and the ALU-bound filter overlap.  Otherwise it launches the
+ * two packs and the filter one after the other.
+ *
+ *   reads, refs    device, n_pairs rows of m ASCII bytes; row i starts at
+ *                  reads + i * stride (refs likewise).
+ *   stride         bytes between rows, >= m.
+ *   n_pairs, m     number of pairs, 1 <= m <= SHOUJI_MAX_M.
+ *   E              0 <= E <= SHOUJI_MAX_E.
+ *   packed_reads,  device, shouji_packed_words(n_pairs, m) words each, 8-byte
+ *   packed_refs    aligned: written with the packed sequences (as
+ *                  shouji_pack, 'N' encoded as 'G').
+ *   out_accept     device uint32[ceil(n_pairs / 32)], as shouji_filter.
+ *   out_count      device uint8[n_pairs], or NULL, as shouji_filter.
+ * Errors: SHOUJI_EINVAL for NULL pointers (with n_pairs > 0), misaligned
+ * packed arrays, m, stride or E out of range; SHOUJI_ECUDA on a launch
+ * failure.  The fused kernel's waits are bounded (about a second) and a wait
+ * that runs out is counted for shouji_wait_failures().
+ */
+shouji_status shouji_pack_filter(const uint8_t *reads, const uint8_t *refs, uint64_t stride,
+                                 size_t n_pairs, uint32_t m, int E, uint32_t *packed_reads,
+                                 uint32_t *packed_refs, uint32_t *out_accept, uint8_t *out_count,
+                                 void *stream);
 
 /*
  * shouji_count -- local and semi-global ("glocal") counting.

@@ -24,6 +24,7 @@ __all__ = [
     "load_library", "shouji_status_string", "shouji_last_cuda_error", "shouji_wait_failures",
     "shouji_selftest_pack_wait",
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
+    "shouji_pack_filter",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
     "Batch", "Server", "shouji_count", "COUNT_GLOBAL", "COUNT_LOCAL", "COUNT_GLOCAL_START",
@@ -70,6 +71,8 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_filter.argtypes = [vp, vp, vp, vp, u32, sz, ctypes.c_int, vp, vp, vp, vp, vp]
     lib.shouji_filter.restype = ctypes.c_int
     lib.shouji_magnet.argtypes = [vp, vp, vp, vp, u32, sz, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.shouji_pack_filter.argtypes = [vp, vp, u64, sz, u32, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.shouji_pack_filter.restype = ctypes.c_int
     lib.shouji_magnet.restype = ctypes.c_int
     lib.shouji_compact_workspace_size.argtypes = [sz]
     lib.shouji_compact_workspace_size.restype = sz
@@ -220,6 +223,36 @@ def shouji_filter(reads, refs, m: int, n_pairs: int, E: int, *, reads_nmask=None
                              _ptr(out_count), _ptr(out_vectors), _stream(stream)),
            "shouji_filter")
     return out_accept, out_count, out_vectors
+
+
+def shouji_pack_filter(reads, refs, m: int, E: int, *, n: int | None = None,
+                       stride: int | None = None, packed_reads=None, packed_refs=None,
+                       out_accept=None, out_count=None, count: bool = True, stream=None):
+    """Pack both ASCII sets and filter them (one fused kernel where it
+    applies).  ``reads``/``refs``: CUDA uint8, (n, stride) or flat with ``n``
+    and ``stride``.  Returns ``(packed_reads, packed_refs, accept_words,
+    count)``."""
+    torch = _torch()
+    lib = load_library()
+    if reads.dim() == 2:
+        n = reads.shape[0] if n is None else n
+        stride = reads.shape[1] if stride is None else stride
+    assert n is not None and stride is not None
+    dev = reads.device
+    words = max(1, lib.shouji_packed_words(n, m))
+    if packed_reads is None:
+        packed_reads = torch.empty(words, dtype=torch.int32, device=dev)
+    if packed_refs is None:
+        packed_refs = torch.empty(words, dtype=torch.int32, device=dev)
+    if out_accept is None:
+        out_accept = torch.empty(max(1, (n + 31) // 32), dtype=torch.int32, device=dev)
+    if out_count is None and count:
+        out_count = torch.empty(max(1, n), dtype=torch.uint8, device=dev)
+    _check(lib.shouji_pack_filter(_ptr(reads), _ptr(refs), stride, n, m, E, _ptr(packed_reads),
+                                  _ptr(packed_refs), _ptr(out_accept), _ptr(out_count),
+                                  _stream(stream)),
+           "shouji_pack_filter")
+    return packed_reads, packed_refs, out_accept, out_count
 
 
 def shouji_magnet(reads, refs, m: int, n_pairs: int, E: int, *, reads_nmask=None,

@@ -117,6 +117,45 @@ shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
     return cuda_status(launch_filter(a, E, (cudaStream_t)stream));
 }
 
+shouji_status shouji_pack_filter(const uint8_t *reads, const uint8_t *refs, uint64_t stride,
+                                 size_t n_pairs, uint32_t m, int E, uint32_t *packed_reads,
+                                 uint32_t *packed_refs, uint32_t *out_accept, uint8_t *out_count,
+                                 void *stream)
+{
+    if (m < 1 || m > SHOUJI_MAX_M || stride < m || E < 0 || E > SHOUJI_MAX_E)
+        return SHOUJI_EINVAL;
+    if (n_pairs == 0)
+        return SHOUJI_OK;
+    if (!reads || !refs || !packed_reads || !packed_refs || !out_accept)
+        return SHOUJI_EINVAL;
+    if ((uintptr_t)packed_reads % 8 || (uintptr_t)packed_refs % 8)
+        return SHOUJI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (stride == m && (uintptr_t)reads % 16 == 0 && (uintptr_t)refs % 16 == 0 &&
+        pack_filter_fusable((int)m, E)) {
+        const cudaError_t f = launch_pack_filter(reads, refs, n_pairs, (int)m, E, packed_reads,
+                                                 packed_refs, out_accept, out_count, s);
+        if (f != cudaErrorNotSupported)
+            return cuda_status(f);
+    }
+    cudaError_t e = launch_pack(reads, stride, n_pairs, (int)m, packed_reads, nullptr, s);
+    if (e == cudaSuccess)
+        e = launch_pack(refs, stride, n_pairs, (int)m, packed_refs, nullptr, s);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    FilterArgs a;
+    a.reads = reinterpret_cast<const uint2 *>(packed_reads);
+    a.refs = reinterpret_cast<const uint2 *>(packed_refs);
+    a.reads_n = a.refs_n = nullptr;
+    a.E_per_pair = nullptr;
+    a.accept = out_accept;
+    a.count = out_count;
+    a.vectors = nullptr;
+    a.n_pairs = n_pairs;
+    a.m = (int)m;
+    return cuda_status(launch_filter(a, E, s));
+}
+
 size_t shouji_compact_workspace_size(size_t n_pairs)
 {
     return n_pairs ? compact_workspace_bytes(n_pairs) : 0;

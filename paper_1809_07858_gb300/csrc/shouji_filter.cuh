@@ -196,6 +196,18 @@ struct View {
     int m;
 };
 
+// Loads of packed words: through the read-only cache, or (COHERENT) as plain
+// loads, for words that another warp of the same CTA wrote earlier in the
+// same kernel.
+template <bool COHERENT, class T>
+__device__ __forceinline__ T ldp(const T *p)
+{
+    if constexpr (COHERENT)
+        return *p;
+    else
+        return __ldg(p);
+}
+
 // Map columns that a chunk hands to the next one: window c needs columns
 // c..c+3, so consecutive chunks of U windows share 3 columns per diagonal.
 // Keeping them in registers saves 3 of every U+3 map evaluations; for large
@@ -222,7 +234,7 @@ struct Carry {
 //           absent and per-pair thresholds.
 // With a carry, the chunk evaluates the U columns c0+3..c0+U+2 and takes
 // c0..c0+2 from the carry; without, it evaluates all U+3 columns c0..c0+U+2.
-template <int E, int U, bool BOUNDS, int MASKS>
+template <int E, int U, bool BOUNDS, int MASKS, bool COHERENT = false>
 __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[E + 1], int c0,
                                       Carry<E> &carry, uint32_t &s0, uint32_t &s1, uint32_t &s2,
                                       uint32_t (&C)[8])
@@ -239,21 +251,21 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
     for (int k = 0; k < NC; ++k) {
         const int p = c0 + K0 + k;
         const bool ok = !BOUNDS || p < v.m;
-        const uint2 w = ok ? __ldg(v.rf + (size_t)p * 32) : make_uint2(0u, 0u);
+        const uint2 w = ok ? ldp<COHERENT>(v.rf + (size_t)p * 32) : make_uint2(0u, 0u);
         th[k] = w.x;
         tl[k] = w.y;
         if constexpr (MASKS != 0)
-            tx[k] = (ok && nm) ? __ldg(v.rfn + (size_t)p * 32) : 0u;
+            tx[k] = (ok && nm) ? ldp<COHERENT>(v.rfn + (size_t)p * 32) : 0u;
     }
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
         const int q = c0 + K0 - E + i;
         const bool ok = !BOUNDS || (q >= 0 && q < v.m);
-        const uint2 w = ok ? __ldg(v.rd + (size_t)q * 32) : make_uint2(0u, 0u);
+        const uint2 w = ok ? ldp<COHERENT>(v.rd + (size_t)q * 32) : make_uint2(0u, 0u);
         rh[i] = w.x;
         rl[i] = w.y;
         if constexpr (MASKS != 0)
-            rx[i] = (ok && nm) ? __ldg(v.rdn + (size_t)q * 32) : 0u;
+            rx[i] = (ok && nm) ? ldp<COHERENT>(v.rdn + (size_t)q * 32) : 0u;
     }
 
     // Mismatch bits of diagonal d at evaluated column k (column c0+K0+k).
@@ -357,7 +369,7 @@ __device__ __forceinline__ void chunk(const View &v, const uint32_t (&inactive)[
 }
 
 // Columns 0..2 of every diagonal: the carry the first chunk starts from.
-template <int E, int MASKS>
+template <int E, int MASKS, bool COHERENT = false>
 __device__ __forceinline__ void carry_prologue(const View &v, const uint32_t (&inactive)[E + 1],
                                                Carry<E> &carry)
 {
@@ -369,12 +381,13 @@ __device__ __forceinline__ void carry_prologue(const View &v, const uint32_t (&i
                 const int q = p - d;
                 uint32_t x = ~0u;
                 if (p < v.m && q >= 0 && q < v.m) {
-                    const uint2 t = __ldg(v.rf + (size_t)p * 32);
-                    const uint2 r = __ldg(v.rd + (size_t)q * 32);
+                    const uint2 t = ldp<COHERENT>(v.rf + (size_t)p * 32);
+                    const uint2 r = ldp<COHERENT>(v.rd + (size_t)q * 32);
                     x = (t.x ^ r.x) | (t.y ^ r.y);
                     if constexpr (MASKS != 0) {
                         if (v.rfn)
-                            x |= __ldg(v.rfn + (size_t)p * 32) | __ldg(v.rdn + (size_t)q * 32);
+                            x |= ldp<COHERENT>(v.rfn + (size_t)p * 32) |
+                                 ldp<COHERENT>(v.rdn + (size_t)q * 32);
                     }
                     if constexpr (MASKS == 2)
                         x |= inactive[d < 0 ? -d : d];
@@ -387,7 +400,7 @@ __device__ __forceinline__ void carry_prologue(const View &v, const uint32_t (&i
 
 // The whole filter for one group of 32 pairs: every window of the group's
 // m columns; C receives the bit-sliced 8-bit counts of ones.
-template <int E, int U, int MASKS>
+template <int E, int U, int MASKS, bool COHERENT = false>
 __device__ __forceinline__ void filter_group(const View &v, const uint32_t (&inactive)[E + 1],
                                              uint32_t (&C)[8])
 {
@@ -398,13 +411,13 @@ __device__ __forceinline__ void filter_group(const View &v, const uint32_t (&ina
         C[i] = 0u;
     const int m = v.m;
     Carry<E> carry;
-    carry_prologue<E, MASKS>(v, inactive, carry);
+    carry_prologue<E, MASKS, COHERENT>(v, inactive, carry);
     constexpr int K0 = Carry<E>::kOn ? 3 : 0;
     for (int c0 = 0; c0 < m; c0 += U) {
         if ((c0 + K0 - E >= 0) && (c0 + U + 2 + E < m))
-            chunk<E, U, false, MASKS>(v, inactive, c0, carry, s0, s1, s2, C);
+            chunk<E, U, false, MASKS, COHERENT>(v, inactive, c0, carry, s0, s1, s2, C);
         else
-            chunk<E, U, true, MASKS>(v, inactive, c0, carry, s0, s1, s2, C);
+            chunk<E, U, true, MASKS, COHERENT>(v, inactive, c0, carry, s0, s1, s2, C);
     }
 }
 

@@ -22,9 +22,26 @@ shouji_status cuda_status(cudaError_t e);
 // Launchers (argument checks are done by the C-ABI layer).
 cudaError_t launch_pack(const uint8_t *seqs, uint64_t stride, size_t n, int m,
                         uint32_t *packed, uint32_t *nmask, cudaStream_t s);
-// Synchronizes the device, then reads and resets the count of pack staging
-// waits that ran out.
+// Synchronizes the device, then reads and resets the count of bounded
+// device waits that ran out (pack staging and the fused pack + filter).
 cudaError_t take_wait_failures(uint32_t *count);
+
+// Largest threshold of the fused pack + filter kernel (its filter warps
+// have 128 registers).
+#define SHOUJI_FUSED_MAX_E 5
+// Whether the fused kernel takes length m and threshold E (the two staging
+// rings must hold at least two 256-row blocks each).
+bool pack_filter_fusable(int m, int E);
+// Pack of both sets and the filter in one kernel; rows contiguous (stride
+// m) on 16-byte boundaries, no N masks or per-pair thresholds (checked by
+// the caller).  cudaErrorNotSupported, with nothing launched, when the
+// kernel does not apply (pack_filter_fusable, or a compiled register count
+// other than the one its register split assumes).
+cudaError_t launch_pack_filter(const uint8_t *reads, const uint8_t *refs, size_t n, int m, int E,
+                               uint32_t *packed_r, uint32_t *packed_t, uint32_t *accept,
+                               uint8_t *count, cudaStream_t s);
+// Reads and resets the fused kernel's count of waits that ran out (no sync).
+cudaError_t take_fused_wait_failures(uint32_t *count);
 // Runs the pack on 1024 sequences with every staging wait made to run out;
 // writes the failures counted.
 cudaError_t selftest_pack_wait(uint32_t *failures);

@@ -273,7 +273,10 @@ cudaError_t take_wait_failures(uint32_t *count)
         const unsigned int zero = 0;
         e = cudaMemcpyToSymbol(g_pack_wait_failures, &zero, sizeof zero);
     }
-    *count = v;
+    uint32_t fused = 0;
+    if (e == cudaSuccess)
+        e = take_fused_wait_failures(&fused);
+    *count = v + fused;
     return e;
 }
 

@@ -33,15 +33,16 @@ __device__ __forceinline__ uint32_t n_bytes(uint32_t w)
 // lane0 .. lane0+LANES-1 of a tile.  A thread owns (lane, 4 consecutive
 // positions); a warp covers LANES lanes x 32/LANES position quads.
 // ALIGNED: rs % 4 == 0, so every 4-position word of a row is word-aligned.
+// The items are shared out among nthreads threads, this one being number tid.
 template <bool WITH_N, bool ALIGNED, int LANES = 8>
-__device__ __forceinline__ void pack_transpose(const uint32_t *__restrict__ sm, int m, int rs,
-                                               size_t tile, int lane0,
-                                               uint32_t *__restrict__ packed,
-                                               uint32_t *__restrict__ nmask, int rot_step,
-                                               int nthreads)
+__device__ __forceinline__ void pack_transpose_by(const uint32_t *__restrict__ sm, int m, int rs,
+                                                  size_t tile, int lane0,
+                                                  uint32_t *__restrict__ packed,
+                                                  uint32_t *__restrict__ nmask, int rot_step,
+                                                  int nthreads, int tid)
 {
     const int J = (m + 3) >> 2;
-    for (int item = threadIdx.x; item < LANES * J; item += nthreads) {
+    for (int item = tid; item < LANES * J; item += nthreads) {
         const int l = item % LANES, j = item / LANES;
         const int rot = (rot_step * l) & 31;     // visit sequence (s + rot) % 32 at step s
         uint32_t yh[4], yl[4], yn[4];
@@ -86,6 +87,72 @@ __device__ __forceinline__ void pack_transpose(const uint32_t *__restrict__ sm, 
             }
         }
     }
+}
+
+// pack_transpose_by for 8 lanes of rows with an odd number W = m / 4 of
+// words (m % 8 == 4), no N mask.  Lane l visits its 32 sequences in 8 groups
+// of 4 consecutive rows, starting at group l: step k = 4q + v reads sequence
+// 4((q + l) % 8) + v.  The 8 lanes x 4 position quads of a warp then read 32
+// distinct banks (4W * g mod 32 takes 8 distinct values over the 8 groups g
+// when W is odd), the row address is found once per 4 words, and each
+// base's bits are shifted straight to their place (a left shift where
+// possible) and merged with one mask-and-or per plane.  The output words are
+// rotated back by 4l, as in pack_transpose_by.
+__device__ __forceinline__ void pack_transpose_w_odd(const uint32_t *__restrict__ sm, int m,
+                                                     size_t tile, int lane0,
+                                                     uint32_t *__restrict__ packed,
+                                                     int nthreads, int tid)
+{
+    constexpr int LANES = 8;
+    const int W = m >> 2;
+    for (int item = tid; item < LANES * W; item += nthreads) {
+        const int l = item % LANES, j = item / LANES;
+        const uint32_t *lane_rows = sm + 32 * l * W + j;  // word j of the lane's first row
+        uint32_t yh[4], yl[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            uint32_t h = 0, lo = 0;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const uint32_t *grp = lane_rows + ((2 * t + half + l) & 7) * 4 * W;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int u = 4 * half + v;  // bit of each byte that step 8t + u fills
+                    const uint32_t w = grp[v * W];
+                    // bit 2 (hi) and bit 1 (lo) of each byte, moved to bit u
+                    const uint32_t xh = u >= 2 ? w << (u - 2) : w >> (2 - u);
+                    const uint32_t xl = u >= 1 ? w << (u - 1) : w >> 1;
+                    h |= xh & (0x01010101u << u);
+                    lo |= xl & (0x01010101u << u);
+                }
+            }
+            yh[t] = h;
+            yl[t] = lo;
+        }
+        uint32_t H[4], L[4];
+        transpose4x4(yh[0], yh[1], yh[2], yh[3], H);
+        transpose4x4(yl[0], yl[1], yl[2], yl[3], L);
+        const int rot = 4 * l;  // bit k holds sequence (k + 4l) % 32: rotate left by 4l
+        const int lane = lane0 + l;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const size_t wi = (tile * (size_t)m + 4 * j + q) * 32 + lane;
+            reinterpret_cast<uint2 *>(packed)[wi] =
+                make_uint2(__funnelshift_l(H[q], H[q], rot), __funnelshift_l(L[q], L[q], rot));
+        }
+    }
+}
+
+// pack_transpose_by with the threads of the CTA in threadIdx.x order.
+template <bool WITH_N, bool ALIGNED, int LANES = 8>
+__device__ __forceinline__ void pack_transpose(const uint32_t *__restrict__ sm, int m, int rs,
+                                               size_t tile, int lane0,
+                                               uint32_t *__restrict__ packed,
+                                               uint32_t *__restrict__ nmask, int rot_step,
+                                               int nthreads)
+{
+    pack_transpose_by<WITH_N, ALIGNED, LANES>(sm, m, rs, tile, lane0, packed, nmask, rot_step,
+                                              nthreads, (int)threadIdx.x);
 }
 
 // Per-lane rotation step c with c * (rs/4) = 32/lanes (mod 32) when such a c
@@ -138,6 +205,11 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 }
 // Arrives once and announces `bytes` more to come from bulk copies; with
 // bytes == 0 the arrival alone completes the phase.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(a) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
@@ -153,13 +225,17 @@ __device__ __forceinline__ void bulk_copy_g2s(void *smem_dst, const void *gsrc, 
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
         ::"r"(d), "l"(gsrc), "r"(bytes), "r"(b) : "memory");
 }
+// One test of the phase; while it is incomplete the thread may sleep in the
+// instruction, for at most about kSuspendNs (it wakes when the phase
+// completes), so waiting warps take no issue slots from working ones.
+constexpr uint32_t kSuspendNs = 100000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
     uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
                  " selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+                 : "=r"(ok) : "r"(a), "r"(parity), "n"(kSuspendNs) : "memory");
     return ok != 0;
 }
 __device__ __forceinline__ uint64_t globaltimer_ns()
@@ -169,8 +245,8 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
     return t;
 }
 // Waits for the phase of `bar` with the given parity to complete; gives up
-// (false) after about a second, or after 2^26 polls should the timer stand
-// still.
+// (false) after about a second, or after 2^26 tests should the timer stand
+// still (a test sleeps at most kSuspendNs, so that is the later bound).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
     if (mbar_try_wait(bar, parity))

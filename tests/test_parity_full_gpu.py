@@ -3,7 +3,9 @@
 30M pairs at m=100 (sweep recipe, E = 0, 5, 10) and 10M pairs at m=150 / 250
 with 'N' bases: every pair is filtered on the GPU and recomputed by the oracle
 (one pair at a time, on all host cores), and the two must match bit for bit on
-every pair; properties that hold for every pair are checked as well.
+every pair; properties that hold for every pair are checked as well.  Without
+N masks the fused pack + filter (shouji_pack_filter, the benchmark's step) is
+checked the same way, and its packed words against shouji_pack's.
 """
 import os
 import numpy as np
@@ -20,12 +22,21 @@ THREADS = max(1, os.cpu_count() or 1)
 
 
 def run_full(reads, refs, m, E, with_n):
+    """The separate launches (pack, pack, filter, compact) and, without N
+    masks, the fused pack + filter on the same rows."""
     dev = torch.device("cuda:0")
     n = len(reads)
     r = torch.from_numpy(reads).to(dev)
     t = torch.from_numpy(refs).to(dev)
     pr, nr = sj.shouji_pack(r, m, with_n=with_n)
     pt, nt = sj.shouji_pack(t, m, with_n=with_n)
+    fused = None
+    if not with_n:
+        fr, ft, facc, fcnt = sj.shouji_pack_filter(r, t, m, E)
+        torch.cuda.synchronize()
+        same_packing = bool(torch.equal(fr, pr)) and bool(torch.equal(ft, pt))
+        fused = (sj.accept_to_bool(facc, n).cpu().numpy(), fcnt[:n].cpu().numpy(), same_packing)
+        del fr, ft, facc, fcnt
     del r, t
     acc, cnt, _ = sj.shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt)
     idx, n_acc = sj.shouji_compact(acc, n)
@@ -34,14 +45,15 @@ def run_full(reads, refs, m, E, with_n):
     count = cnt[:n].cpu().numpy()
     k = int(n_acc.item())
     survivors = idx[:k].cpu().numpy()
-    return accept, count, survivors
+    assert sj.shouji_wait_failures() == 0
+    return accept, count, survivors, fused
 
 
 def check(reads, refs, m, E, with_n):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     n = len(reads)
-    accept, count, survivors = run_full(reads, refs, m, E, with_n)
+    accept, count, survivors, fused = run_full(reads, refs, m, E, with_n)
     # properties over every pair
     assert (count <= m).all()
     assert (accept == (count <= E)).all()
@@ -52,6 +64,11 @@ def check(reads, refs, m, E, with_n):
     acc_o, cnt_o = oracle.shouji_batch(reads, refs, E, threads=THREADS)
     bad = np.flatnonzero((count != cnt_o) | (accept != acc_o))
     assert bad.size == 0, "%d pairs differ, first %s" % (bad.size, bad[:10])
+    if fused is not None:
+        f_acc, f_cnt, same_packing = fused
+        assert same_packing, "fused pack + filter wrote other packed words"
+        bad = np.flatnonzero((f_cnt != cnt_o) | (f_acc != acc_o))
+        assert bad.size == 0, "fused: %d pairs differ, first %s" % (bad.size, bad[:10])
 
 
 @pytest.mark.parametrize("E", [0, 5, 10])
