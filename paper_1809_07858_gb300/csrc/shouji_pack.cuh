@@ -229,6 +229,25 @@ __device__ __forceinline__ void bulk_copy_g2s(void *smem_dst, const void *gsrc, 
 // instruction, for at most about kSuspendNs (it wakes when the phase
 // completes), so waiting warps take no issue slots from working ones.
 constexpr uint32_t kSuspendNs = 100000;
+// The same bulk copy with an L2 eviction policy (from createpolicy).
+__device__ __forceinline__ void bulk_copy_g2s_hint(void *smem_dst, const void *gsrc,
+                                                   uint32_t bytes, uint64_t *bar,
+                                                   uint64_t policy)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;\n"
+        ::"r"(d), "l"(gsrc), "r"(bytes), "r"(b), "l"(policy) : "memory");
+}
+// L2 policy: lines brought in go first when L2 needs room (data read once).
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);

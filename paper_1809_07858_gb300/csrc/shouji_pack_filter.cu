@@ -9,22 +9,24 @@
 //  - 16 producer warps in two independent groups of 8 stream the CTA's range
 //    of tiles (1024 pairs each).  A tile is 8 blocks of 256 sequences (4 of
 //    reads, then 4 of refs); group g takes the blocks i = g (mod 2).  Each
-//    group has its own ring of shared-memory buffers filled by bulk copies
-//    (one per block, completing on the buffer's mbarrier) and its own named
-//    barrier, so the two groups' transpositions overlap.  A block costs a
-//    group about the latency of one transposition item plus two barriers,
-//    whatever its size, so two groups double the pack rate.
+//    group has its own named barrier and its own ring of shared-memory
+//    buffers, filled by bulk copies (one per block, completing on the
+//    buffer's mbarrier; the ASCII lines are marked to leave L2 first), so the
+//    two groups' transpositions overlap.  A block costs a group about the
+//    latency of one transposition item plus two barriers, whatever its size,
+//    so two groups double the pack rate.
 //  - 8 consumer warps filter the tiles already packed, each taking every 8th
 //    tile of the range.
 // A tile is handed over through two mbarriers per consumer: `ready` (all 512
 // producer threads arrive once their words of the tile are written) and
-// `freed` (the consumer's 32 threads arrive once they have seen it ready), so
-// the producers run at most two tiles ahead of a consumer and the parity of
-// each barrier phase is never ambiguous.  The producers wait only on
-// consumer steps that depend on phases the producers completed before, so
-// the hand-over cannot deadlock; every wait is bounded all the same (about a
-// second), and a wait that runs out ends the warps concerned and is counted
-// for shouji_wait_failures().
+// `freed` (the consumer's 32 threads arrive once they have filtered it).  The
+// producers complete a consumer's tile k only after its tile k-1 is freed, so
+// they run at most one tile ahead of each consumer (the packed words in
+// flight stay within L2) and the parity of each barrier phase is never
+// ambiguous.  The producers wait only on consumer steps that depend on
+// phases the producers completed before, so the hand-over cannot deadlock;
+// every wait is bounded all the same (about a second), and a wait that runs
+// out ends the warps concerned and is counted for shouji_wait_failures().
 //
 // Registers: the CTA is launched with 768 threads at 80 registers (61,440 of
 // the SM's 65,536).  The producers give theirs down to 56 and the consumers
@@ -118,6 +120,9 @@ __device__ void produce(const FusedArgs &a, uint8_t *ring, uint64_t *full, uint6
     auto src_of = [&](size_t i, size_t seq0) -> const uint8_t * {
         return ((i / kHalfBlocks) % 2 ? a.refs : a.reads) + seq0 * (size_t)a.m;
     };
+    // The ASCII rows are read once: their lines leave L2 first, so that the
+    // packed words written for the filter warps stay there until read.
+    const uint64_t policy = l2_evict_first_policy();
     auto issue = [&](size_t j) {  // one thread: the group's j-th block
         const size_t i = j * kGroups + g;
         size_t seq0;
@@ -126,7 +131,8 @@ __device__ void produce(const FusedArgs &a, uint8_t *ring, uint64_t *full, uint6
         const int b = (int)(j % (size_t)a.ring);
         mbar_arrive_expect_tx(&myfull[b], bytes);
         if (bytes)
-            bulk_copy_g2s(myring + (size_t)b * a.buf_bytes, src_of(i, seq0), bytes, &myfull[b]);
+            bulk_copy_g2s_hint(myring + (size_t)b * a.buf_bytes, src_of(i, seq0), bytes,
+                               &myfull[b], policy);
     };
 
     size_t issued = 0;  // jobs whose copies have been issued (same in every thread)
@@ -204,10 +210,11 @@ __device__ void consume(const FusedArgs &a, uint64_t *ready, uint64_t *freed, si
                 atomicAdd(&g_fused_wait_failures, 1u);
             return;
         }
-        mbar_arrive(&freed[w]);
         const size_t grp = t * kLanes + lane;  // this thread's group of 32 pairs
-        if (grp >= n_groups)
+        if (grp >= n_groups) {
+            mbar_arrive(&freed[w]);
             continue;
+        }
         const size_t base = t * (size_t)m * kLanes + lane;
         filt::View v;
         v.rd = reinterpret_cast<const uint2 *>(a.packed_r) + base;
@@ -239,6 +246,7 @@ __device__ void consume(const FusedArgs &a, uint64_t *ready, uint64_t *freed, si
                     a.count[first + b] = (uint8_t)(cw[b >> 2] >> (8 * (b & 3)));
             }
         }
+        mbar_arrive(&freed[w]);  // done with tile t
     }
 }
 
