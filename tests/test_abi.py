@@ -78,6 +78,22 @@ def test_host_argument_checks_return_einval():
                              None, None, None) == EINVAL
     assert lib.shouji_magnet(None, None, None, None, 100, 0, 5, None, None, None, None, None) == OK
     assert lib.shouji_wait_failures(None) == EINVAL
+    # pack_filter: m, stride or E out of range, nulls, misaligned packed arrays; n = 0 is OK
+    u64, sz = ctypes.c_uint64, ctypes.c_size_t
+    pf = lib.shouji_pack_filter
+    assert pf(fake, fake, u64(100), sz(10), 0, 5, fake, fake, fake, None, None) == EINVAL
+    assert pf(fake, fake, u64(300), sz(10), 256, 5, fake, fake, fake, None, None) == EINVAL
+    assert pf(fake, fake, u64(99), sz(10), 100, 5, fake, fake, fake, None, None) == EINVAL
+    assert pf(fake, fake, u64(100), sz(10), 100, -1, fake, fake, fake, None, None) == EINVAL
+    assert pf(fake, fake, u64(100), sz(10), 100, 32, fake, fake, fake, None, None) == EINVAL
+    assert pf(None, fake, u64(100), sz(10), 100, 5, fake, fake, fake, None, None) == EINVAL
+    assert pf(fake, None, u64(100), sz(10), 100, 5, fake, fake, fake, None, None) == EINVAL
+    assert pf(fake, fake, u64(100), sz(10), 100, 5, None, fake, fake, None, None) == EINVAL
+    assert pf(fake, fake, u64(100), sz(10), 100, 5, fake, None, fake, None, None) == EINVAL
+    assert pf(fake, fake, u64(100), sz(10), 100, 5, fake, fake, None, None, None) == EINVAL
+    assert pf(fake, fake, u64(100), sz(10), 100, 5, ctypes.c_void_p(0x1004), fake, fake, None,
+              None) == EINVAL
+    assert pf(None, None, u64(100), sz(0), 100, 5, None, None, None, None, None) == OK
     assert lib.shouji_selftest_pack_wait(None) == EINVAL
     # compact: short or misaligned workspace, too many pairs, nulls
     assert lib.shouji_compact(fake, 1000, fake, fake, fake, 0, None) == EINVAL
