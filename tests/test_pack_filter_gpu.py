@@ -1,9 +1,10 @@
 """shouji_pack_filter: both packs and the filter in one call (a fused
-warp-specialized kernel when rows are contiguous on 16-byte boundaries and
-E <= 8, the separate launches otherwise).  Accept bits and counts are compared
-with the oracle pair by pair, and the packed words with an independent unpack
-of the ASCII input, across lengths, thresholds, ragged sizes, sizes that give
-a CTA one tile or hundreds, and the fallback layouts."""
+warp-specialized kernel when rows are contiguous on 16-byte boundaries, E <= 5
+and m is within the staging rings; the separate launches otherwise).  Accept
+bits and counts are compared with the oracle pair by pair, and the packed
+words with an independent unpack of the ASCII input, across lengths,
+thresholds, ragged sizes, sizes that give a CTA one tile or hundreds, and the
+fallback layouts."""
 import numpy as np
 import pytest
 
@@ -75,7 +76,7 @@ def pairs(n, m, E, seed):
                        far_fraction=0.5)
 
 
-@pytest.mark.parametrize("E", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("E", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_thresholds_m100(E):
     reads, refs = pairs(70_001, 100, E, 100 + E)
     check(reads, refs, 100, E)
@@ -98,6 +99,20 @@ def test_layouts_of_the_fused_producer(m):
     E = 5 if m > 12 else 2
     reads, refs = pairs(3_000 + m, m, E, 400 + m)
     check(reads, refs, m, E)
+
+
+@pytest.mark.parametrize("m", [1, 4, 12, 33, 36, 64, 65, 100, 124, 128, 131, 132, 133, 140])
+@pytest.mark.parametrize("E", [6, 8])
+def test_above_the_fused_thresholds(m, E):
+    """Thresholds above 5 take the separate launches at every length."""
+    reads, refs = pairs(5_000 + m, m, E, 700 + m + E)
+    check(reads, refs, m, E)
+
+
+@pytest.mark.parametrize("n", [1, 1025, 155_649, 311_297, 1_000_001])
+def test_above_the_fused_thresholds_ragged_sizes(n):
+    reads, refs = pairs(n, 100, 7, 800 + n % 1000)
+    check(reads, refs, 100, 7, packing=n < 500_000)
 
 
 @pytest.mark.parametrize("n", [1, 31, 32, 33, 255, 256, 257, 1023, 1024, 1025, 4097, 155_648,
@@ -136,3 +151,31 @@ def test_zero_pairs_and_bad_arguments():
     assert lib.shouji_pack_filter(p, p, 100, 10, 100, 5, p + 4, p, p, None, None) == 1
     assert lib.shouji_pack_filter(None, p, 100, 10, 100, 5, p, p, p, None, None) == 1
     del x
+
+
+def test_without_counts_on_a_side_stream_with_reused_outputs():
+    """Counts left out (NULL), a non-default stream, and the same output
+    buffers reused across calls that take the fused kernel (E = 5, 2) and the
+    separate launches (E = 7, 12) in turn."""
+    d = dev()
+    n, m = 50_001, 100
+    words = sj.shouji_packed_words(n, m)
+    pr = torch.full((words,), -1, dtype=torch.int32, device=d)
+    pt = torch.full((words,), -1, dtype=torch.int32, device=d)
+    acc = torch.full(((n + 31) // 32,), -1, dtype=torch.int32, device=d)
+    side = torch.cuda.Stream(device=d)
+    for E in (5, 7, 12, 2):
+        reads, refs = pairs(n, m, E, 600 + E)
+        r = torch.from_numpy(reads).to(d)
+        t = torch.from_numpy(refs).to(d)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            _, _, _, cnt = sj.shouji_pack_filter(r, t, m, E, packed_reads=pr, packed_refs=pt,
+                                                 out_accept=acc, count=False, stream=side)
+        side.synchronize()
+        assert cnt is None
+        assert sj.shouji_wait_failures() == 0
+        acc_o, _ = oracle.shouji_batch(reads, refs, E, threads=8)
+        assert (accept_bits(acc, n) == acc_o).all()
+        assert (unpack_planes(pr.cpu().numpy(), n, m) == CODE[reads]).all()
+        assert (unpack_planes(pt.cpu().numpy(), n, m) == CODE[refs]).all()
