@@ -71,9 +71,9 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_filter.argtypes = [vp, vp, vp, vp, u32, sz, ctypes.c_int, vp, vp, vp, vp, vp]
     lib.shouji_filter.restype = ctypes.c_int
     lib.shouji_magnet.argtypes = [vp, vp, vp, vp, u32, sz, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.shouji_magnet.restype = ctypes.c_int
     lib.shouji_pack_filter.argtypes = [vp, vp, u64, sz, u32, ctypes.c_int, vp, vp, vp, vp, vp]
     lib.shouji_pack_filter.restype = ctypes.c_int
-    lib.shouji_magnet.restype = ctypes.c_int
     lib.shouji_compact_workspace_size.argtypes = [sz]
     lib.shouji_compact_workspace_size.restype = sz
     lib.shouji_compact.argtypes = [vp, sz, vp, vp, vp, sz, vp]
@@ -346,12 +346,16 @@ def filter_pairs(reads, refs, E: int, *, with_n: bool | None = None, E_per_pair=
     """Pack and filter (n, m) uint8 CUDA tensors of reads and references.
 
     Returns ``(accept_bool[n], count_uint8[n])``.  ``with_n`` defaults to
-    checking whether any 'N' is present.
+    checking whether any 'N' is present.  Without N masks or per-pair
+    thresholds this is one ``shouji_pack_filter`` call.
     """
     n, m = reads.shape
     assert refs.shape == reads.shape
     if with_n is None:
         with_n = bool(((reads == 78).any() | (refs == 78).any()).item())
+    if not with_n and E_per_pair is None:
+        _, _, acc, cnt = shouji_pack_filter(reads, refs, m, E, stream=stream)
+        return accept_to_bool(acc, n), cnt[:n]
     pr, nr = shouji_pack(reads, m, with_n=with_n, stream=stream)
     pt, nt = shouji_pack(refs, m, with_n=with_n, stream=stream)
     acc, cnt, _ = shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
