@@ -159,7 +159,8 @@ def gpu_index_for(local_rank: int) -> int:
 
 def workload_config(n):
     return {"workload": "sweep m=100 E=5: %d pairs, half near (k~U{0..5}) half far (k~U{6..25}), "
-                        "ASCII resident in HBM; step = pack reads + pack refs + filter + compact" % n,
+                        "ASCII resident in HBM; step = pack reads and refs + filter (one fused "
+                        "kernel on the GPU) + compact" % n,
             "n_pairs": n, "m": M, "E": E,
             "l2": "inputs larger than L2 (%.1f GB ASCII per step); no flush" % (2 * n * M / 1e9)}
 
