@@ -5,9 +5,10 @@ of length m = 100 at threshold E = 5, half near (k ~ U{0..5} edits) and half
 far (k ~ U{6..25}), ASCII reads and references resident in HBM (6 GB, larger
 than L2, so no flush is needed between steps).  One step is the whole hot path
 over the batch: shouji_pack_filter (both packs and the filter in one
-warp-specialized kernel), then shouji_compact.  ``e2e`` runs the same batch through the host pipeline
-(shouji_pipeline_run: pinned host buffers in, accept bits, counts and survivor
-indices out), with every copy inside the timed region.
+warp-specialized kernel), then shouji_compact.  ``e2e`` runs the same batch
+through the host pipeline (shouji_pipeline_run: pinned host buffers in, accept
+bits, counts and survivor indices out), with every copy inside the timed
+region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
