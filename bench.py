@@ -36,7 +36,6 @@ UNIT = "pairs/s"
 N_PAIRS = 30_000_000
 M = 100
 E = 5
-ALU_LANES_PER_SM_CLK = 64   # LOP3/SHF/PRMT issue rate of the integer ALU pipe per SM
 # DRAM bytes per filter launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture, keyed by the hash of the filter kernel source it was
 # taken on; scaled to a 30M-pair launch.  Reported as null once the kernel
@@ -47,22 +46,53 @@ FUSED_TRAFFIC = {"a30b69b8e80798a7": 7.232e9}  # profiles/pack_filter_kernel_m10
 FUSED_SOURCES = ("shouji_pack_filter.cu", "shouji_pack.cuh", "shouji_filter.cuh")
 
 
-def fused_bytes_per_pair(m: int) -> float:
-    """Algorithmic DRAM bytes per pair of the fused pack + filter: both ASCII
-    rows in (2m), both packed rows out (2 x m/4), an accept bit and a count
-    byte out."""
-    return 2 * m + 2 * (m / 4) + 1 / 8 + 1
+def step_bytes_per_pair(m: int) -> float:
+    """Algorithmic DRAM bytes per pair of the step from ASCII: both rows in
+    (2m), an accept bit and a count byte out."""
+    return 2 * m + 1 / 8 + 1
 
 
-def alu_ops_per_pair(m: int, E: int) -> float:
+def packed_out_bytes_per_pair(m: int) -> float:
+    """Bytes per pair of the packed rows that shouji_pack_filter also writes
+    (2 x m/4): an output of the API, kept for reuse, not work of the filter."""
+    return 2 * (m / 4)
+
+
+def filter_bytes_per_pair(m: int, nmask: bool = False) -> float:
+    """Algorithmic DRAM bytes per pair of the filter alone: both packed rows
+    in (2 bits per base each, plus 1 bit per base of N mask each), an accept
+    bit and a count byte out."""
+    return 2 * m / 4 + (2 * m / 8 if nmask else 0) + 1 / 8 + 1
+
+
+def alu_ops_per_pair(m: int, E: int, nmask: bool = False) -> float:
     """Algorithmic integer lane-ops per pair of the bit-sliced formulation.
 
     Per window and 32 pairs: map 2(2E+1), segment full adders 2(2E+1),
     2E-1 candidate offers of 12 ops, the strict main-diagonal offer 18, the
     Shouji-vector update 8 and the counter 4 -> 32E + 22 (E >= 1; 16 at E=0).
+    N masks add one OR per map cell: + (2E+1).
     """
     per_window = (32 * E + 22) if E >= 1 else 16
+    if nmask:
+        per_window += 2 * E + 1
     return m * per_window / 32.0
+
+
+def alu_peak(dev):
+    """Measured integer issue rates (lane-ops per SM clock, shouji_alu_probe)
+    and the ALU peak they give: SMs x LOP3 rate x maximum SM clock."""
+    import torch
+
+    import paper_1809_07858_gb300 as sj
+    torch.cuda.synchronize(dev)
+    rates = {op: round(sj.shouji_alu_probe(op), 2) for op in sj.PROBE_OPS}
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    return {"lane_ops_per_sm_clk": rates, "sms": sms, "sm_max_mhz": sm_max,
+            "peak": sms * rates["lop3"] * sm_max * 1e6, "unit": "lane-ops/s",
+            "basis": "SMs x measured LOP3 lane-ops per SM clock (shouji_alu_probe) x max SM clock"}
 
 
 def source_hash(names=("shouji_filter.cuh",)) -> str:
@@ -238,18 +268,180 @@ def run_batched(args, dev, peak_ops):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.batched_steps
+    stages = b.timing()
     invalid = b.invalid()
     b.close()
     del d_reads, d_refs
     torch.cuda.empty_cache()
     achieved = ops / (ms * 1e-3)
+    filt_ms = stages["filters"]
     return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.batched_steps,
             "workload": "%d pairs, lengths 40%% 100 / 40%% 150 / 20%% 250, E uniform 2..12, "
                         "unsorted, stride 256, one CUDA-graph launch per batch (tuned)" % n,
             "invalid": invalid,
+            "stages_ms": stages,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                          "unit": "lane-ops/s", "frac": achieved / peak_ops,
-                         "scope": "whole batch step (bucketing, packing, filters, gather)"}}
+                         "scope": "whole batch step (bucketing, packing, filters, gather)",
+                         "filters_frac": ops / (filt_ms * 1e-3) / peak_ops if filt_ms > 0 else None}}
+
+
+def run_batched_uniform(args, dev, peak_ops, h_reads, h_refs):
+    """The batched persistent kernel on a uniform batch: the headline's pairs
+    (m=100, E=5), rows at stride 112 (16-byte boundaries), one CUDA-graph
+    launch per batch.  The graph records CUDA events around each stage and
+    around the E=5 filter kernel; the kernel's roofline fraction uses its own
+    recorded time."""
+    import numpy as np
+    import torch
+
+    import paper_1809_07858_gb300 as sj
+    n = h_reads.shape[0]
+    stride = 112
+    d_reads = torch.zeros((n, stride), dtype=torch.uint8, device=dev)
+    d_refs = torch.zeros((n, stride), dtype=torch.uint8, device=dev)
+    d_reads[:, :M].copy_(h_reads, non_blocking=True)
+    d_refs[:, :M].copy_(h_refs, non_blocking=True)
+    d_lens = torch.full((n,), M, dtype=torch.int16, device=dev)
+    d_E = torch.full((n,), E, dtype=torch.uint8, device=dev)
+    acc = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.uint8, device=dev)
+    b = sj.Batch(n, M, E, E)
+    b.tune(d_reads, d_refs, d_lens, d_E)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        b.run(d_reads, d_refs, d_lens, d_E, out_accept=acc, out_count=cnt)
+    torch.cuda.synchronize(dev)
+    kernel_ms, stage_list = [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.batched_steps):
+        b.run(d_reads, d_refs, d_lens, d_E, out_accept=acc, out_count=cnt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.batched_steps
+    # the kernel's own time: the graph's event nodes around it, run by run
+    for _ in range(args.batched_steps):
+        b.run(d_reads, d_refs, d_lens, d_E, out_accept=acc, out_count=cnt)
+        st = b.timing()
+        stage_list.append(st)
+        kernel_ms.append(st["filter_E"][E])
+    b.close()
+    accepted = int(np.unpackbits(acc.cpu().numpy().view(np.uint8)).sum())
+    del d_reads, d_refs
+    torch.cuda.empty_cache()
+    k_ms = statistics.median(kernel_ms)
+    ops = alu_ops_per_pair(M, E) * n
+    stages = {k: statistics.median(x[k] for x in stage_list)
+              for k in ("graph", "bucketing", "pack", "filters", "finalize")}
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.batched_steps,
+            "workload": "%d pairs m=%d E=%d (the headline's pairs), rows at stride %d, one "
+                        "CUDA-graph launch per batch (tuned)" % (n, M, E, stride),
+            "accepted": accepted, "stages_ms": stages,
+            "kernel": "batch_filter_kernel<%d>" % E, "kernel_ms": k_ms,
+            "kernel_ms_runs": [round(x, 4) for x in kernel_ms],
+            "roofline": {"bound": "alu", "achieved": ops / (k_ms * 1e-3), "peak": peak_ops,
+                         "unit": "lane-ops/s", "frac": ops / (k_ms * 1e-3) / peak_ops,
+                         "scope": "the E=%d filter kernel alone, timed by CUDA events the graph "
+                                  "records around it" % E,
+                         "ops_per_pair": alu_ops_per_pair(M, E)},
+            "graph_frac": ops / (ms * 1e-3) / peak_ops}
+
+
+def run_sweep(args, dev, peak_ops, hbm_peak):
+    """The E sweep (m=100): for each E, 30M pairs of the sweep recipe at that
+    E, packed once, then the filter alone on the packed pairs, resident in
+    HBM (CUDA events over --sweep-steps launches)."""
+    import numpy as np
+    import torch
+
+    import paper_1809_07858_gb300 as sj
+    from paper_1809_07858_gb300 import synth
+    n = args.sweep_n
+    out = []
+    h_r = np.empty((n, M), np.uint8)
+    h_t = np.empty((n, M), np.uint8)
+    d_r = torch.empty((n, M), dtype=torch.uint8, device=dev)
+    d_t = torch.empty((n, M), dtype=torch.uint8, device=dev)
+    pr = torch.empty(sj.shouji_packed_words(n, M), dtype=torch.int32, device=dev)
+    pt = torch.empty_like(pr)
+    acc = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for e in args.sweep_E:
+        synth.workload("sweep", n, E=e, out=(h_r, h_t))
+        d_r.copy_(torch.from_numpy(h_r))
+        d_t.copy_(torch.from_numpy(h_t))
+        sj.shouji_pack(d_r, M, packed=pr, stream=stream)
+        sj.shouji_pack(d_t, M, packed=pt, stream=stream)
+        for _ in range(2):
+            sj.shouji_filter(pr, pt, M, n, e, out_accept=acc, out_count=cnt, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.sweep_steps):
+            sj.shouji_filter(pr, pt, M, n, e, out_accept=acc, out_count=cnt, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.sweep_steps
+        ops = alu_ops_per_pair(M, e) * n
+        accepted = int(np.unpackbits(acc.cpu().numpy().view(np.uint8)).sum())
+        out.append({"E": e, "m": M, "n_pairs": n, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
+                    "accepted": accepted, "alu_frac": ops / (ms * 1e-3) / peak_ops,
+                    "hbm_frac": filter_bytes_per_pair(M) * n / (ms * 1e-3) / 1e9 / hbm_peak})
+    del d_r, d_t, pr, pt
+    torch.cuda.empty_cache()
+    return {"kernel": "shouji_filter (packed pairs resident in HBM)",
+            "workload": "sweep recipe per E: %d pairs m=%d, half near k~U{0..E}, half far "
+                        "k~U{E+1..25}, seed 1000+E" % (n, M),
+            "steps": args.sweep_steps, "points": out}
+
+
+def run_long(args, dev, peak_ops, hbm_peak):
+    """Long reads with 'N' (m = 150 and 250, 0.1% 'N' on each side): per
+    (m, E), pairs of the long recipe packed with N masks, then the masked
+    filter alone on the packed pairs, resident in HBM."""
+    import numpy as np
+    import torch
+
+    import paper_1809_07858_gb300 as sj
+    from paper_1809_07858_gb300 import synth
+    n = args.long_n
+    stream = torch.cuda.current_stream(dev)
+    out = []
+    for m, e in ((150, 7), (150, 15), (250, 12), (250, 15)):
+        h_r, h_t = synth.workload("long", n, E=e, m=m)
+        d_r = torch.from_numpy(h_r).to(dev)
+        d_t = torch.from_numpy(h_t).to(dev)
+        pr, nr = sj.shouji_pack(d_r, m, with_n=True, stream=stream)
+        pt, nt = sj.shouji_pack(d_t, m, with_n=True, stream=stream)
+        del d_r, d_t
+        acc = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+        cnt = torch.empty(n, dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            sj.shouji_filter(pr, pt, m, n, e, reads_nmask=nr, refs_nmask=nt, out_accept=acc,
+                             out_count=cnt, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.sweep_steps):
+            sj.shouji_filter(pr, pt, m, n, e, reads_nmask=nr, refs_nmask=nt, out_accept=acc,
+                             out_count=cnt, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.sweep_steps
+        ops = alu_ops_per_pair(m, e, nmask=True) * n
+        accepted = int(np.unpackbits(acc.cpu().numpy().view(np.uint8)).sum())
+        out.append({"m": m, "E": e, "n_pairs": n, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
+                    "accepted": accepted, "alu_frac": ops / (ms * 1e-3) / peak_ops,
+                    "hbm_frac": filter_bytes_per_pair(m, True) * n / (ms * 1e-3) / 1e9 / hbm_peak})
+        del pr, pt, nr, nt, acc, cnt, h_r, h_t
+        torch.cuda.empty_cache()
+    return {"kernel": "shouji_filter with N masks (packed pairs resident in HBM)",
+            "workload": "long recipe per (m, E): %d pairs, near k~U{0..E}, far "
+                        "k~U{E+1..ceil(m/4)}, 0.1%% N per base and side, seed 2000+m+E" % n,
+            "steps": args.sweep_steps, "points": out}
 
 
 def run_magnet(args, dev, packed_r, packed_t, n, shouji_accept):
@@ -286,11 +478,28 @@ def run_magnet(args, dev, packed_r, packed_t, n, shouji_accept):
             "accepted_shouji_not_magnet": ones(s_words & ~m_words)}
 
 
+def union_length(spans):
+    total, end = 0.0, -1.0
+    for a, b in sorted(spans):
+        if a > end:
+            total += b - a
+            end = b
+        elif b > end:
+            total += b - end
+            end = b
+    return total
+
+
 def run_served(args, dev):
     """The served form: requests of log-uniform size in [1e3, 1e6] pairs with
-    the batched mix, arriving as a Poisson process at --serve-rate per second,
-    filtered by the server (continuous batching over memory-budgeted slots).
-    Latency = submit to results in host memory."""
+    the batched mix, filtered by the server (continuous batching, admission by
+    device memory).  Three loads: closed loop (the server's capacity), Poisson
+    arrivals at --serve-rate per second (the offered load of the workload),
+    and Poisson arrivals at 80% of the capacity; each with p50/p99 latency
+    (submit to results in host memory) and the overlap of requests on the GPU
+    (summed GPU time of the requests over the time any was on the GPU).  The
+    same at capacity with the reference segments resident on the device
+    (requests send reads and offsets only)."""
     import threading
 
     import numpy as np
@@ -306,58 +515,94 @@ def run_served(args, dev):
                 stride=256, out=(h_reads, h_refs))
     h_lens = torch.from_numpy(lens.astype(np.int16)).pin_memory()
     h_E = torch.from_numpy(Es).pin_memory()
-    rng = np.random.default_rng(99)
-    n_req = max(1, int(args.serve_rate * args.serve_seconds))
-    sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=n_req)).astype(np.int64)
-    gaps = rng.exponential(1.0 / args.serve_rate, size=n_req)
-    offs = rng.integers(0, pool - sizes + 1)
+    h_off = torch.from_numpy(np.arange(pool, dtype=np.int64) * 256).pin_memory()
     ring = 64
     outs = [(torch.empty(31_251, dtype=torch.int32, pin_memory=True),
              torch.empty(1_000_000, dtype=torch.uint8, pin_memory=True)) for _ in range(ring)]
     budget = int(args.serve_budget_gb * (1 << 30))
     srv = sj.Server(1_000_000, 250, 2, 12, max_stride=256, memory_budget=budget,
                     max_slots=args.serve_slots)
-    slots, per_slot = srv.info()
-    ids = [None] * n_req
-    ready = [threading.Event() for _ in range(n_req)]
-    lat = [0.0] * n_req
-    free = threading.Semaphore(ring)
+    ref_id = srv.add_reference(h_refs.view(-1))
+    rng = np.random.default_rng(99)
 
-    def submitter():
-        t_next = time.perf_counter()
+    def submit(i, size, off, resident):
+        a, c = outs[i % ring]
+        if resident:
+            return srv.submit_at(h_reads[off:off + size], ref_id, h_off[off:off + size],
+                                 h_lens[off:off + size], h_E[off:off + size], a, c,
+                                 n_pairs=size, stride=256)
+        return srv.submit(h_reads[off:off + size], h_refs[off:off + size], h_lens[off:off + size],
+                          h_E[off:off + size], a, c, n_pairs=size, stride=256)
+
+    def drive(n_req, rate=None, inflight=None, resident=False):
+        """rate: Poisson arrivals per second; inflight: closed loop with that
+        many requests outstanding."""
+        sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=n_req)).astype(np.int64)
+        offs = rng.integers(0, pool - sizes + 1)
+        gaps = rng.exponential(1.0 / rate, size=n_req) if rate else None
+        ids = [None] * n_req
+        ready = [threading.Event() for _ in range(n_req)]
+        res = [None] * n_req
+        free = threading.Semaphore(inflight if inflight else ring)
+
+        def submitter():
+            t_next = time.perf_counter()
+            for i in range(n_req):
+                if rate:
+                    t_next += gaps[i]
+                    delay = t_next - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                free.acquire()
+                ids[i] = submit(i, int(sizes[i]), int(offs[i]), resident)
+                ready[i].set()
+
+        t0 = time.perf_counter()
+        th = threading.Thread(target=submitter)
+        th.start()
         for i in range(n_req):
-            t_next += gaps[i]
-            delay = t_next - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            free.acquire()
-            a, c = outs[i % ring]
-            o, k = int(offs[i]), int(sizes[i])
-            ids[i] = srv.submit(h_reads[o:o + k], h_refs[o:o + k], h_lens[o:o + k], h_E[o:o + k],
-                                a, c, n_pairs=k, stride=256)
-            ready[i].set()
+            ready[i].wait()
+            res[i] = srv.wait_timed(ids[i], timeout=120)
+            free.release()
+        wall = time.perf_counter() - t0
+        th.join()
+        lat_ms = np.array([r[0] for r in res]) * 1e3
+        spans = [(r[1], r[2]) for r in res]
+        busy = union_length(spans)
+        return {"value": float(sizes.sum()) / wall, "unit": UNIT, "requests": n_req,
+                "duration_s": wall, "p50_ms": float(np.percentile(lat_ms, 50)),
+                "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mean_request_pairs": float(sizes.mean()),
+                "overlap": sum(b - a for a, b in spans) / busy if busy > 0 else None,
+                "gpu_busy_frac": busy / wall}
 
-    t0 = time.perf_counter()
-    th = threading.Thread(target=submitter)
-    th.start()
-    for i in range(n_req):
-        ready[i].wait()
-        lat[i] = srv.wait(ids[i], timeout=120)
-        free.release()
-    t_end = time.perf_counter()
-    th.join()
+    drive(64, inflight=16)                       # warm-up: workers of every class are made
+    drive(32, inflight=16, resident=True)
+    n_cap = max(16, int(args.serve_seconds * 150))
+    cap = drive(n_cap, inflight=args.serve_inflight)
+    cap_res = drive(n_cap, inflight=args.serve_inflight, resident=True)
+    mean_pairs = cap["mean_request_pairs"]
+    n_off = max(8, int(args.serve_rate * args.serve_seconds))
+    offered = drive(n_off, rate=args.serve_rate)
+    rate80 = 0.8 * cap["value"] / mean_pairs
+    at80 = drive(max(8, int(rate80 * args.serve_seconds / 2)), rate=rate80)
+    st = srv.stats()
     srv.close()
-    wall = t_end - t0
-    total = int(sizes.sum())
-    lat_ms = np.array(lat) * 1e3
-    return {"value": total / wall, "unit": UNIT, "requests": n_req, "duration_s": wall,
-            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "mean_request_pairs": float(sizes.mean()),
-            "offered_pairs_per_s": float(sizes.mean() * args.serve_rate),
-            "arrival": "Poisson, %g requests/s; sizes log-uniform in [1e3, 1e6] pairs; "
-                       "lengths 40%% 100 / 40%% 150 / 20%% 250, E uniform 2..12" % args.serve_rate,
-            "slots": slots, "bytes_per_slot": per_slot,
-            "memory_budget_gb": args.serve_budget_gb}
+    for d, r in ((offered, args.serve_rate), (at80, rate80)):
+        d["arrival"] = "Poisson, %.1f requests/s" % r
+        d["offered_pairs_per_s"] = r * mean_pairs
+    return {"value": offered["value"], "unit": UNIT, "p50_ms": offered["p50_ms"],
+            "p99_ms": offered["p99_ms"],
+            "workload": "requests of log-uniform size in [1e3, 1e6] pairs; lengths 40% 100 / 40% "
+                        "150 / 20% 250, E uniform 2..12; rows at stride 256 in pinned host memory",
+            "offered": offered, "capacity": cap,
+            "capacity_pairs_per_s": cap["value"], "at_80pct_capacity": at80,
+            "capacity_resident_refs": cap_res,
+            "memory_budget_gb": args.serve_budget_gb,
+            "peak_used_gb": st["peak_used_bytes"] / (1 << 30),
+            "peak_concurrent_requests": st["peak_busy_workers"],
+            "workers_made": st["workers_made"], "workers_released": st["workers_released"],
+            "closed_loop_inflight": args.serve_inflight}
 
 
 def run_ours(args, world, rank, local):
@@ -389,6 +634,10 @@ def run_ours(args, world, rank, local):
     n_acc = torch.empty(1, dtype=torch.int32, device=dev)
     ws = torch.empty(max(16, sj.shouji_compact_workspace_size(n)), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    alu = alu_peak(dev)
+    peak_ops = alu["peak"]
+    # whether the step's pack + filter is the one fused kernel (else three launches)
+    fused = sj.shouji_pack_filter_fused(d_reads, d_refs, M, E)
 
     ev = {k: [] for k in ("fused0", "fused1", "compact0", "compact1")}
 
@@ -491,29 +740,61 @@ def run_ours(args, world, rank, local):
 
     clocks = clk.summary()
     peaks = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
-    peak_ops = sms * ALU_LANES_PER_SM_CLK * sm_max * 1e6
     ops_launch = alu_ops_per_pair(M, E) * n
     achieved = ops_launch / (filter_ms * 1e-3)
     src = filter_source_hash()
     traffic = FILTER_TRAFFIC.get(src)
     hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
     fused_src = source_hash(FUSED_SOURCES)
-    fused_gbs = fused_bytes_per_pair(M) * n / (fused_ms * 1e-3) / 1e9
+    # The step's roofline: the larger of its two algorithmic lower bounds,
+    # the bytes it must move (ASCII in, accept bits and counts out) at the
+    # measured HBM copy bandwidth and the filter's lane-ops at the measured
+    # integer peak.
+    step_bytes = step_bytes_per_pair(M) * n
+    t_hbm = step_bytes / (hbm_peak * 1e9)
+    t_alu = ops_launch / peak_ops
+    fused_s = fused_ms * 1e-3
+    hbm_frac = step_bytes / fused_s / 1e9 / hbm_peak
+    alu_frac = ops_launch / fused_s / peak_ops
+    with_packed = (step_bytes_per_pair(M) + packed_out_bytes_per_pair(M)) * n
+    if t_hbm >= t_alu:
+        roofline = {"bound": "hbm", "achieved": step_bytes / fused_s / 1e9, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": hbm_frac,
+                    "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roofline = {"bound": "alu", "achieved": ops_launch / fused_s, "peak": peak_ops,
+                    "unit": "lane-ops/s", "frac": alu_frac, "peak_basis": alu["basis"]}
+    # traffic: DRAM bytes per launch from one ncu capture of this kernel source
+    roofline.update({
+        "traffic": FUSED_TRAFFIC.get(fused_src),
+        "kernel": "shouji_pack_filter (%s)" % ("pack_filter_kernel" if fused else
+                                               "separate pack x2 + filter launches"),
+        "fused_kernel": fused,
+        "bytes_per_pair": step_bytes_per_pair(M),
+        "bytes_basis": "2m ASCII in + 1/8 accept + 1 count out per pair",
+        "hbm_frac": hbm_frac, "alu_frac": alu_frac,
+        "alu_ops_per_pair": alu_ops_per_pair(M, E),
+        "with_packed_out": {"bytes_per_pair": step_bytes_per_pair(M) + packed_out_bytes_per_pair(M),
+                            "achieved": with_packed / fused_s / 1e9, "unit": "GB/s",
+                            "frac": with_packed / fused_s / 1e9 / hbm_peak,
+                            "note": "counts the packed rows the call also writes for reuse"},
+        "src": fused_src})
     value = world * n * args.steps / (elapsed_ms * 1e-3)
     e2e_value = world * n * args.e2e_steps / e2e_s
     h2d = 2 * n * M
     d2h = h_acc.numel() * 4 + n + 4 * n_accepted
-    batched = served = magnet = None
+    batched = batched_uniform = served = magnet = sweep = long_reads = None
     if world == 1 and args.magnet_steps > 0:
         magnet = run_magnet(args, dev, packed_r, packed_t, n, accept)
     if world == 1:
         del d_reads, d_refs, packed_r, packed_t, idx
         torch.cuda.empty_cache()
         if args.batched_steps > 0:
+            batched_uniform = run_batched_uniform(args, dev, peak_ops, h_reads, h_refs)
             batched = run_batched(args, dev, peak_ops)
+        if args.sweep_steps > 0:
+            sweep = run_sweep(args, dev, peak_ops, hbm_peak)
+            long_reads = run_long(args, dev, peak_ops, hbm_peak)
         if args.serve_seconds > 0:
             served = run_served(args, dev)
     cpu = None
@@ -542,17 +823,9 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "step_ms": e2e_steps_ms,
                 "path": "shouji_pipeline_run, pinned host buffers, chunks of %d pairs" % args.chunk},
-        "gpu_launches": 4 * args.steps,
-        "roofline": {"bound": "hbm", "achieved": fused_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": fused_gbs / hbm_peak, "traffic": FUSED_TRAFFIC.get(fused_src),
-                     "kernel": "shouji_pack_filter (pack_filter_kernel)",
-                     "bytes_per_pair": fused_bytes_per_pair(M),
-                     "peak_basis": "measured HBM copy bandwidth",
-                     "alu_frac": ops_launch / (fused_ms * 1e-3) / peak_ops,
-                     "alu_basis": "%.2f algorithmic filter lane-ops per pair over %d SMs x %d "
-                                  "lane-ops/clk x %.0f MHz" % (alu_ops_per_pair(M, E), sms,
-                                                               ALU_LANES_PER_SM_CLK, sm_max),
-                     "src": fused_src},
+        "gpu_launches": (4 if fused else 6) * args.steps,
+        "roofline": roofline,
+        "alu_peak": alu,
         "kernels_ms": {"pack_filter": fused_ms, "compact": compact_ms},
         "separate": {"pack_x2_ms": pack_ms, "filter_ms": filter_ms,
                      "filter_roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
@@ -561,7 +834,10 @@ def run_ours(args, world, rank, local):
         "accepted": n_accepted,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "batched_uniform": batched_uniform,
         "batched": batched,
+        "sweep": sweep,
+        "long_reads": long_reads,
         "served": served,
         "magnet": magnet,
     }
@@ -584,11 +860,18 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--batched-n", type=int, default=50_000_000)
-    ap.add_argument("--batched-steps", type=int, default=10, help="0 skips the batched leg")
+    ap.add_argument("--batched-steps", type=int, default=10, help="0 skips the batched legs")
+    ap.add_argument("--sweep-n", type=int, default=30_000_000)
+    ap.add_argument("--long-n", type=int, default=10_000_000)
+    ap.add_argument("--sweep-E", type=lambda v: [int(x) for x in v.split(",")],
+                    default=[0, 2, 5, 8, 10])
+    ap.add_argument("--sweep-steps", type=int, default=10,
+                    help="0 skips the E-sweep and long-read legs")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="0 skips the served leg")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
-    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-inflight", type=int, default=32)
     ap.add_argument("--magnet-steps", type=int, default=5, help="0 skips the MAGNET leg")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -26,8 +26,14 @@
  *   - n = 0 pairs is valid and does nothing.
  *   - Bases are the uppercase ASCII letters A, C, G, T and N.  An 'N' never
  *     matches anything, another 'N' included, when its sequence was packed
- *     with an N mask; without one it is read as 'G'.  Other bytes are not
- *     checked: they are read through their bits 1-2 like the four bases.
+ *     with an N mask.  Without one it is read as 'G', which gives other
+ *     results; every pack without an N mask therefore looks for 'N' bytes
+ *     on the device: shouji_unmasked_n() returns SHOUJI_EINVAL once
+ *     shouji_pack, shouji_pack_filter or the batched and served forms
+ *     without with_n have seen one, and shouji_pipeline_run without with_n
+ *     returns SHOUJI_EINVAL itself.  Other bytes are read
+ *     through their bits 1-2 like the four bases (a byte with bit 3 set,
+ *     such as 'n', is reported like an 'N').
  *
  * Packed ("bit-sliced") sequence layout, produced by shouji_pack and read by
  * shouji_filter.  Sequences are grouped into tiles of SHOUJI_TILE = 1024 =
@@ -97,6 +103,30 @@ size_t shouji_nmask_words(size_t n, uint32_t m);
 shouji_status shouji_wait_failures(uint32_t *count);
 
 /*
+ * shouji_unmasked_n -- whether a pack without an N mask read an 'N'.
+ *
+ * The paper's filter compares bases (Eq. 1); an 'N' (an unknown base) is read
+ * here as matching nothing, another 'N' included, which needs an N mask
+ * (shouji_pack with nmask, shouji_filter with both masks, the batched and
+ * served forms and the host pipeline with with_n).  Without a mask an 'N' has
+ * no 2-bit code of its own and is read as 'G'.  So that such results are
+ * never taken silently, every pack without a mask (shouji_pack,
+ * shouji_pack_filter, the batched and served forms without with_n) checks
+ * its bytes on the device and sets a flag when one holds an 'N'.  This call synchronizes the
+ * device, writes the flag to *seen (1: at least one pack without an N mask
+ * since the last call read an 'N', so its pairs' results differ from the
+ * masked ones; 0: none did), resets it, and returns SHOUJI_EINVAL when it was
+ * set.  The flag is shared by all calls of the process on the device: read
+ * it after the calls whose input is in question, with no other unmasked
+ * pack running.  shouji_pipeline_run (with_n = 0) keeps a flag per pipeline
+ * instead and reports through its own status.
+ *   seen   host, written.
+ * Errors: SHOUJI_EINVAL for NULL seen, and when the flag was set;
+ * SHOUJI_ECUDA when the synchronize or the read fails.
+ */
+shouji_status shouji_unmasked_n(int *seen);
+
+/*
  * shouji_selftest_pack_wait -- exercises the path above without a fault.
  *
  * Packs 1024 sequences of 4 bases (one tile: 4 blocks of 256 rows, one CTA
@@ -109,6 +139,38 @@ shouji_status shouji_wait_failures(uint32_t *count);
  * Errors: SHOUJI_EINVAL for NULL failures; SHOUJI_ECUDA on a CUDA failure.
  */
 shouji_status shouji_selftest_pack_wait(uint32_t *failures);
+
+/*
+ * shouji_alu_probe -- measured issue rate of one integer instruction kind.
+ *
+ * The filter of Sec. 2.2 is computed here as bit-sliced integer logic, 32
+ * pairs per instruction, so its roofline is the issue rate of the GPU's
+ * integer pipes, not a memory or tensor figure.  This call measures that rate on
+ * the current device: one CTA of 1024 threads per SM runs independent
+ * dependency chains of the chosen instruction, and each CTA counts its own
+ * SM cycles around the loop.  The result, in lane-operations per SM clock,
+ * does not depend on the clock the GPU runs at; multiplied by the SM count
+ * and the maximum SM clock it gives the peak rate.
+ *   op    SHOUJI_PROBE_LOP3 (3-input logic), _SHF (funnel shift), _PRMT
+ *         (byte permute), _IADD3 (3-input add), _IMAD (integer
+ *         multiply-add), _POPC (population count), or _LOP3_IMAD (half of
+ *         the chains LOP3, half IMAD: the combined rate of two pipes).
+ *   lane_ops_per_sm_clock  host, written: median over the SMs.
+ * Unlike the compute calls, this one allocates two small device buffers
+ * (freed before it returns) and synchronizes the device.  It takes a few
+ * milliseconds.
+ * Errors: SHOUJI_EINVAL for a NULL output or an unknown op; SHOUJI_ECUDA on
+ * a CUDA failure.
+ */
+#define SHOUJI_PROBE_LOP3 0
+#define SHOUJI_PROBE_SHF 1
+#define SHOUJI_PROBE_PRMT 2
+#define SHOUJI_PROBE_IADD3 3
+#define SHOUJI_PROBE_IMAD 4
+#define SHOUJI_PROBE_POPC 5
+#define SHOUJI_PROBE_LOP3_IMAD 6
+
+shouji_status shouji_alu_probe(int op, double *lane_ops_per_sm_clock);
 
 /*
  * shouji_pack -- ASCII sequences to the packed bit-sliced layout.
@@ -196,7 +258,8 @@ shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
  *   E              0 <= E <= SHOUJI_MAX_E.
  *   packed_reads,  device, shouji_packed_words(n_pairs, m) words each, 8-byte
  *   packed_refs    aligned: written with the packed sequences (as
- *                  shouji_pack, 'N' encoded as 'G').
+ *                  shouji_pack without a mask: 'N' read as 'G', and
+ *                  flagged for shouji_unmasked_n).
  *   out_accept     device uint32[ceil(n_pairs / 32)], as shouji_filter.
  *   out_count      device uint8[n_pairs], or NULL, as shouji_filter.
  * Errors: SHOUJI_EINVAL for NULL pointers (with n_pairs > 0), misaligned
@@ -208,6 +271,21 @@ shouji_status shouji_pack_filter(const uint8_t *reads, const uint8_t *refs, uint
                                  size_t n_pairs, uint32_t m, int E, uint32_t *packed_reads,
                                  uint32_t *packed_refs, uint32_t *out_accept, uint8_t *out_count,
                                  void *stream);
+
+/*
+ * shouji_pack_filter_fused -- whether shouji_pack_filter with these
+ * arguments runs as the one fused kernel (1) or as separate pack and filter
+ * launches (0).  Both give the same results; the query exists so that a
+ * caller (or a benchmark) can tell which kernel it is timing.  The answer
+ * depends on the row layout, m, E and on the compiled kernel itself (its
+ * register split needs an exact register count), so it needs the device.
+ *   reads, refs, stride, m, E  as shouji_pack_filter (nothing is read).
+ *   fused   host, written.
+ * Errors: SHOUJI_EINVAL for NULL fused or m, stride or E out of range;
+ * SHOUJI_ECUDA when the kernel's attributes cannot be read.
+ */
+shouji_status shouji_pack_filter_fused(const uint8_t *reads, const uint8_t *refs,
+                                       uint64_t stride, uint32_t m, int E, int *fused);
 
 /*
  * shouji_count -- local and semi-global ("glocal") counting.
@@ -316,13 +394,17 @@ shouji_status shouji_compact(const uint32_t *accept, size_t n_pairs,
  * routine.
  *
  * Its workspace is a fixed 64 KB __device__ array inside libshouji.so, held
- * on every GPU that loads the library until the process exits.  The first
- * call on each device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  Every call on a device shares the one array:
- * two calls whose work overlaps on the GPU (e.g. on two streams) race and
- * may return wrong indices; serialize them.  The array keeps the last
- * call's contents, and nothing in it needs to start at zero.
+ * in every CUDA context that loads the library's kernels until that context
+ * is destroyed (for the primary context: until the process exits or the
+ * device is reset).  The array's device address belongs to a context, so the
+ * first call in each context (the primary context of a device, a new one
+ * after cudaDeviceReset, or a context the program created with the driver
+ * API) looks it up (cudaGetSymbolAddress) with that context current and
+ * caches it under the context's id; make that first call before any stream
+ * capture.  Every call in a context shares the one array: two calls whose
+ * work overlaps on the GPU (e.g. on two streams) race and may return wrong
+ * indices; serialize them.  The array keeps the last call's contents, and
+ * nothing in it needs to start at zero.
  *
  *   accept, n_pairs, out_idx, out_n, stream: as shouji_compact.
  * Errors: SHOUJI_EINVAL for n_pairs > SHOUJI_NOALLOC_MAX_PAIRS (2^29) or
@@ -357,7 +439,10 @@ shouji_status shouji_compact_noalloc(const uint32_t *accept, size_t n_pairs,
  *
  * shouji_pipeline_run filters n_pairs pairs and returns when all results
  * are in host memory (it synchronizes its own streams only).  Host buffers
- * should be pinned (cudaHostAlloc) for the copies to overlap.
+ * should be pinned (cudaHostAlloc) for the copies to overlap.  A pipeline
+ * created without with_n keeps a flag of its own, like the one of
+ * shouji_unmasked_n, and returns SHOUJI_EINVAL, with every result written,
+ * when one of the run's sequences held an 'N' (read as 'G').
  *   reads, refs  host, n_pairs rows of m bytes, row i at + i * stride.
  *   E            0 <= E <= SHOUJI_MAX_E.
  *   accept       host uint32[ceil(n_pairs / 32)] (layout of shouji_filter).
@@ -417,14 +502,25 @@ void shouji_pipeline_destroy(shouji_pipeline *pipeline);
  *   out_accept    uint32[ceil(n_pairs / 32)] (layout of shouji_filter).
  *   out_count     uint8[n_pairs] or NULL.
  * A pair whose length or threshold is out of range is rejected (accept 0,
- * count 255) and counted by shouji_batch_invalid.  Before it writes a new
- * argument block, a run waits until the previous run of the same object has
- * started on the GPU; one object runs one batch at a time, and concurrent
- * batches need one object each.
+ * count 255) and counted by shouji_batch_invalid.  The object holds two
+ * argument blocks, each with its own captured graph, and alternates between
+ * them: a run waits only for the run two before it (which used the same
+ * block) to have finished, so the host can queue a run while the previous
+ * one is still on the GPU.  All runs of one object share its device
+ * buffers: queue them on one stream (they then run one after the other);
+ * concurrent batches need one object each.
  * Errors: SHOUJI_EINVAL (nothing launched), SHOUJI_ECUDA.
  *
  * shouji_batch_invalid waits for the last run and returns its number of
  * rejected out-of-range pairs.
+ *
+ * shouji_batch_timing waits for the last run and writes the durations, in
+ * milliseconds, that the graph itself recorded (event nodes between its
+ * stages): ms[0] the whole graph, ms[1] bucketing (classify, scan, fill,
+ * scatter), ms[2] the gather-pack, ms[3] the filters (all thresholds, from
+ * the fork to the last join), ms[4] finalize, and ms[5 + E] the filter
+ * kernel of threshold E alone (-1 for thresholds outside [e_min, e_max], and
+ * everywhere before the first run).  n must be at least SHOUJI_BATCH_TIMES.
  *
  * shouji_batch_tune is the autotuner.  It runs the bucketing and packing of
  * the given batch, then times every launch shape of each threshold's filter
@@ -443,13 +539,38 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min,
                                   int e_max, int with_n, const char *tune_cache,
                                   shouji_batch **out);
 
+/* Device bytes that shouji_batch_create with these arguments allocates (0
+ * for arguments it would reject); for planning device memory. */
+size_t shouji_batch_device_bytes(size_t max_pairs, uint32_t max_m, int e_min, int e_max,
+                                 int with_n);
+
 shouji_status shouji_batch_run(shouji_batch *batch, const uint8_t *reads,
                                const uint8_t *refs, uint64_t stride,
                                const uint16_t *lens, const uint8_t *E_per_pair,
                                size_t n_pairs, uint32_t *out_accept,
                                uint8_t *out_count, void *stream);
 
+/*
+ * shouji_batch_run_at -- shouji_batch_run with the references taken from a
+ * text kept on the device (e.g. a reference genome loaded once): pair i
+ * compares read i (row reads + i * stride) with the lens[i] bytes of
+ * ref_text starting at ref_offsets[i] (device uint64[n_pairs]; any byte
+ * offset, ref_offsets[i] + lens[i] within the text).  In a read mapper the
+ * candidate locations of a read are offsets into the reference (Sec. 3.6 of
+ * the paper filters the candidate pairs a mapper produces); the references
+ * then need no copy per batch.  Everything else is as shouji_batch_run.
+ */
+shouji_status shouji_batch_run_at(shouji_batch *batch, const uint8_t *reads, uint64_t stride,
+                                  const uint8_t *ref_text, const uint64_t *ref_offsets,
+                                  const uint16_t *lens, const uint8_t *E_per_pair,
+                                  size_t n_pairs, uint32_t *out_accept, uint8_t *out_count,
+                                  void *stream);
+
 shouji_status shouji_batch_invalid(shouji_batch *batch, uint64_t *n_invalid);
+
+#define SHOUJI_BATCH_TIMES (5 + SHOUJI_MAX_E + 1)
+
+shouji_status shouji_batch_timing(shouji_batch *batch, float *ms, int n);
 
 shouji_status shouji_batch_tune(shouji_batch *batch, const uint8_t *reads,
                                 const uint8_t *refs, uint64_t stride,
@@ -465,41 +586,95 @@ void shouji_batch_destroy(shouji_batch *batch);
  *
  * The paper integrates the filter into read mappers, which produce candidate
  * pairs continuously and keep only the pairs the filter accepts (Sec. 3.6,
- * Table 15).  A server takes requests from any host thread.  A dispatcher
- * thread admits them in arrival order into slots.  A slot is a batch object
- * (one CUDA graph) with its own stream and device buffers.  An admitted
- * request is copied in, filtered and copied out on its slot's stream, so
- * requests admitted while others are on the GPU run concurrently with them;
- * a finished slot takes the next queued request at once.
+ * Table 15).  A server takes requests from any host thread; a dispatcher
+ * thread admits them in arrival order by device memory.  A worker is a
+ * batch object (one CUDA graph per run) with its own stream and staging
+ * buffers, sized for a capacity class of 4096 x 2^k pairs (the last class is
+ * max_request_pairs).  A request runs on the smallest free worker that holds
+ * it; when none is free, a worker of its class is made if it fits in the
+ * memory budget next to everything already held (idle workers are released,
+ * least recently used first, to make room), and otherwise the request waits
+ * for a running one to finish.  A request thus holds device memory in
+ * proportion to its size, and requests admitted while others are on the GPU
+ * run concurrently with them.  Making or releasing a worker allocates or
+ * frees device memory, which can briefly synchronize the device.
  *
- * shouji_server_create makes slots on the current device until the next
- * one would exceed memory_budget bytes (the first slot measures the cost of
- * one) or max_slots exist, then starts the dispatcher.
- *   max_request_pairs  largest request; max_m, e_min, e_max, with_n,
+ * shouji_server_create starts the dispatcher; workers are made on demand.
+ *   max_request_pairs  largest request (< 2^31); max_m, e_min, e_max, with_n,
  *                      tune_cache: as shouji_batch_create.
  *   max_stride         largest row stride of a request (>= max_m).
- * Errors: SHOUJI_EINVAL; SHOUJI_ENOMEM (not even one slot fits the budget
- * or the device); SHOUJI_ECUDA.
+ *   memory_budget      device bytes the server may hold (workers and
+ *                      resident references).
+ *   max_slots          most workers at once (requests on the GPU at once).
+ * Errors: SHOUJI_EINVAL; SHOUJI_ENOMEM (the budget cannot hold one worker
+ * for max_request_pairs); SHOUJI_ECUDA.
  *
- * shouji_server_info: number of slots and device bytes of one slot.
+ * shouji_server_info: number of workers held now, and device bytes of a
+ * worker for max_request_pairs.  shouji_server_stats_read: the memory and
+ * admission counters below.
  *
- * shouji_server_submit queues one request and returns at once with its id.
- * Host buffers, as shouji_batch_run's device ones (reads/refs rows of
- * `stride` bytes, lens, E_per_pair, accept, optional count), must stay
- * valid and untouched until shouji_server_wait returns for the id.  Pinned
- * host buffers let the copies run asynchronously.
+ * shouji_server_add_reference copies a reference text (any bytes, e.g. a
+ * chromosome in ASCII) to the device, where it stays until the server is
+ * destroyed, counted against the budget; writes its id.  Requests then name
+ * their reference segments by offset into it instead of sending them.
+ * Errors: SHOUJI_EINVAL; SHOUJI_ENOMEM when it would leave no room for one
+ * worker of the largest class; SHOUJI_ECUDA.
+ *
+ * shouji_server_submit_request queues one request and returns at once with
+ * its id.  The request (copied) names:
+ *   reads          host rows of the reads, row i at reads + i * stride;
+ *   refs           host rows of the reference segments (same stride), or
+ *                  NULL to take pair i's segment from the resident text
+ *                  ref_id at byte ref_offsets[i] (host uint64[n_pairs]; every
+ *                  segment must lie inside the text, else SHOUJI_EINVAL);
+ *   lens, E_per_pair, n_pairs  host arrays and count, as shouji_batch_run;
+ *   accept, count  outputs (layout of shouji_filter; count may be NULL):
+ *                  host memory, or device memory of the server's device with
+ *                  SHOUJI_SERVE_DEVICE_RESULTS in flags (written by the
+ *                  filter directly, no copy back).
+ * Host buffers must stay valid and untouched until the request is waited
+ * for.  Pinned host buffers let the copies run asynchronously; results for
+ * host buffers that are not pinned go through pinned staging of the
+ * worker's and are copied over when the request completes.
+ * shouji_server_submit is the same for host rows of reads and references.
  * Errors: SHOUJI_EINVAL (bad argument or the server is stopping).
  *
  * shouji_server_wait blocks until the request is done or timeout_s seconds
  * have passed (SHOUJI_ETIMEOUT; the request stays queued or in flight and
  * can be waited for again).  On completion it writes the latency, from
  * submit to completion in seconds, into latency_s (when not NULL), forgets
- * the id, and returns the request's status.
+ * the id, and returns the request's status.  shouji_server_wait_timed also
+ * writes times[1] and times[2]: when the request's work started and ended on
+ * the GPU, in seconds since the server was created (CUDA events around its
+ * copies and its graph), from which the overlap of requests on the device
+ * can be measured; times[0] is the latency.
  *
  * shouji_server_destroy finishes every queued and in-flight request, stops
  * the dispatcher and frees everything.
  */
 typedef struct shouji_server shouji_server;
+
+#define SHOUJI_SERVE_DEVICE_RESULTS 1
+
+typedef struct {
+    const uint8_t *reads;
+    const uint8_t *refs;
+    uint64_t stride;
+    uint32_t ref_id;
+    const uint64_t *ref_offsets;
+    const uint16_t *lens;
+    const uint8_t *E_per_pair;
+    size_t n_pairs;
+    uint32_t *accept;
+    uint8_t *count;
+    int flags;
+} shouji_server_request;
+
+typedef struct {
+    uint64_t budget_bytes, used_bytes, peak_used_bytes, reference_bytes;
+    int workers, busy_workers, peak_busy_workers, queued;
+    uint64_t admitted, workers_made, workers_released;
+} shouji_server_stats;
 
 shouji_status shouji_server_create(size_t max_request_pairs, uint32_t max_m,
                                    uint64_t max_stride, int e_min, int e_max,
@@ -510,6 +685,15 @@ shouji_status shouji_server_create(size_t max_request_pairs, uint32_t max_m,
 shouji_status shouji_server_info(shouji_server *server, int *slots,
                                  uint64_t *bytes_per_slot);
 
+shouji_status shouji_server_stats_read(shouji_server *server, shouji_server_stats *out);
+
+shouji_status shouji_server_add_reference(shouji_server *server, const uint8_t *text,
+                                          uint64_t bytes, uint32_t *ref_id);
+
+shouji_status shouji_server_submit_request(shouji_server *server,
+                                           const shouji_server_request *request,
+                                           uint64_t *request_id);
+
 shouji_status shouji_server_submit(shouji_server *server, const uint8_t *reads,
                                    const uint8_t *refs, uint64_t stride,
                                    const uint16_t *lens,
@@ -519,6 +703,9 @@ shouji_status shouji_server_submit(shouji_server *server, const uint8_t *reads,
 
 shouji_status shouji_server_wait(shouji_server *server, uint64_t request_id,
                                  double timeout_s, double *latency_s);
+
+shouji_status shouji_server_wait_timed(shouji_server *server, uint64_t request_id,
+                                       double timeout_s, double *times);
 
 void shouji_server_destroy(shouji_server *server);
 

@@ -22,13 +22,13 @@ SHOUJI_NOALLOC_MAX_PAIRS = 1 << 29
 __all__ = [
     "ShoujiError", "SHOUJI_TILE", "SHOUJI_MAX_M", "SHOUJI_MAX_E", "LIB_PATH",
     "load_library", "shouji_status_string", "shouji_last_cuda_error", "shouji_wait_failures",
-    "shouji_selftest_pack_wait",
+    "shouji_selftest_pack_wait", "shouji_alu_probe", "PROBE_OPS", "shouji_unmasked_n",
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
-    "shouji_pack_filter",
+    "shouji_pack_filter", "shouji_pack_filter_fused",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
     "Batch", "Server", "shouji_count", "COUNT_GLOBAL", "COUNT_LOCAL", "COUNT_GLOCAL_START",
-    "COUNT_GLOCAL_END", "shouji_magnet", "magnet_pairs",
+    "COUNT_GLOCAL_END", "shouji_magnet", "magnet_pairs", "SERVE_DEVICE_RESULTS",
 ]
 
 COUNT_GLOBAL, COUNT_LOCAL, COUNT_GLOCAL_START, COUNT_GLOCAL_END = 0, 1, 2, 3
@@ -62,6 +62,10 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_wait_failures.restype = ctypes.c_int
     lib.shouji_selftest_pack_wait.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
     lib.shouji_selftest_pack_wait.restype = ctypes.c_int
+    lib.shouji_unmasked_n.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    lib.shouji_unmasked_n.restype = ctypes.c_int
+    lib.shouji_alu_probe.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.shouji_alu_probe.restype = ctypes.c_int
     lib.shouji_packed_words.argtypes = [sz, u32]
     lib.shouji_packed_words.restype = sz
     lib.shouji_nmask_words.argtypes = [sz, u32]
@@ -74,6 +78,9 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_magnet.restype = ctypes.c_int
     lib.shouji_pack_filter.argtypes = [vp, vp, u64, sz, u32, ctypes.c_int, vp, vp, vp, vp, vp]
     lib.shouji_pack_filter.restype = ctypes.c_int
+    lib.shouji_pack_filter_fused.argtypes = [vp, vp, u64, u32, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int)]
+    lib.shouji_pack_filter_fused.restype = ctypes.c_int
     lib.shouji_compact_workspace_size.argtypes = [sz]
     lib.shouji_compact_workspace_size.restype = sz
     lib.shouji_compact.argtypes = [vp, sz, vp, vp, vp, sz, vp]
@@ -87,6 +94,8 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_batch_run.restype = ctypes.c_int
     lib.shouji_batch_invalid.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.shouji_batch_invalid.restype = ctypes.c_int
+    lib.shouji_batch_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.shouji_batch_timing.restype = ctypes.c_int
     lib.shouji_batch_tune.argtypes = [vp, vp, vp, u64, vp, vp, sz, vp, vp, ctypes.c_char_p, vp]
     lib.shouji_batch_tune.restype = ctypes.c_int
     lib.shouji_batch_destroy.argtypes = [vp]
@@ -102,6 +111,19 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_server_submit.restype = ctypes.c_int
     lib.shouji_server_wait.argtypes = [vp, u64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.shouji_server_wait.restype = ctypes.c_int
+    lib.shouji_server_wait_timed.argtypes = [vp, u64, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_double)]
+    lib.shouji_server_wait_timed.restype = ctypes.c_int
+    lib.shouji_server_submit_request.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.shouji_server_submit_request.restype = ctypes.c_int
+    lib.shouji_server_add_reference.argtypes = [vp, vp, u64, ctypes.POINTER(ctypes.c_uint32)]
+    lib.shouji_server_add_reference.restype = ctypes.c_int
+    lib.shouji_server_stats_read.argtypes = [vp, vp]
+    lib.shouji_server_stats_read.restype = ctypes.c_int
+    lib.shouji_batch_run_at.argtypes = [vp, vp, u64, vp, vp, vp, vp, sz, vp, vp, vp]
+    lib.shouji_batch_run_at.restype = ctypes.c_int
+    lib.shouji_batch_device_bytes.argtypes = [sz, u32, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.shouji_batch_device_bytes.restype = sz
     lib.shouji_server_destroy.argtypes = [vp]
     lib.shouji_server_destroy.restype = None
     lib.shouji_count.argtypes = [vp, u32, sz, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
@@ -139,6 +161,27 @@ def shouji_selftest_pack_wait() -> int:
     c = ctypes.c_uint32(0)
     _check(load_library().shouji_selftest_pack_wait(ctypes.byref(c)), "shouji_selftest_pack_wait")
     return c.value
+
+
+def shouji_unmasked_n() -> bool:
+    """Synchronize the device; whether a pack without an N mask has read an
+    'N' (as 'G') since the last call, and reset that flag."""
+    v = ctypes.c_int(0)
+    st = load_library().shouji_unmasked_n(ctypes.byref(v))
+    if st not in (0, 1) or (st == 1 and not v.value):
+        _check(st, "shouji_unmasked_n")
+    return bool(v.value)
+
+
+PROBE_OPS = {"lop3": 0, "shf": 1, "prmt": 2, "iadd3": 3, "imad": 4, "popc": 5, "lop3+imad": 6}
+
+
+def shouji_alu_probe(op: str = "lop3") -> float:
+    """Measured lane-operations per SM clock of one integer instruction kind
+    (see ``PROBE_OPS``) on the current device; synchronizes the device."""
+    r = ctypes.c_double(0.0)
+    _check(load_library().shouji_alu_probe(PROBE_OPS[op], ctypes.byref(r)), "shouji_alu_probe")
+    return r.value
 
 
 def shouji_packed_words(n: int, m: int) -> int:
@@ -255,6 +298,16 @@ def shouji_pack_filter(reads, refs, m: int, E: int, *, n: int | None = None,
     return packed_reads, packed_refs, out_accept, out_count
 
 
+def shouji_pack_filter_fused(reads, refs, m: int, E: int, *, stride: int | None = None) -> bool:
+    """Whether ``shouji_pack_filter`` on these rows runs as the one fused
+    kernel (True) or as separate pack and filter launches (False)."""
+    stride = (reads.shape[1] if reads.dim() == 2 else m) if stride is None else stride
+    f = ctypes.c_int(0)
+    _check(load_library().shouji_pack_filter_fused(_ptr(reads), _ptr(refs), stride, m, E,
+                                                   ctypes.byref(f)), "shouji_pack_filter_fused")
+    return bool(f.value)
+
+
 def shouji_magnet(reads, refs, m: int, n_pairs: int, E: int, *, reads_nmask=None,
                   refs_nmask=None, E_per_pair=None, out_accept=None, out_count=None,
                   count: bool = True, out_vectors=None, vectors: bool = False,
@@ -341,23 +394,40 @@ def accept_to_bool(accept_words, n_pairs: int):
     return bits.reshape(-1)[:n_pairs].bool()
 
 
+def _pack_pairs(reads, refs, m: int, with_n, stream):
+    """Pack both sets; ``with_n=None`` packs without N masks first and packs
+    again with them when the device saw an 'N' (shouji_unmasked_n)."""
+    if with_n is None:
+        shouji_unmasked_n()  # clear the flag
+        pr, _ = shouji_pack(reads, m, stream=stream)
+        pt, _ = shouji_pack(refs, m, stream=stream)
+        if not shouji_unmasked_n():
+            return pr, None, pt, None
+        with_n = True
+    pr, nr = shouji_pack(reads, m, with_n=with_n, stream=stream)
+    pt, nt = shouji_pack(refs, m, with_n=with_n, stream=stream)
+    return pr, nr, pt, nt
+
+
 def filter_pairs(reads, refs, E: int, *, with_n: bool | None = None, E_per_pair=None,
                  stream=None):
     """Pack and filter (n, m) uint8 CUDA tensors of reads and references.
 
-    Returns ``(accept_bool[n], count_uint8[n])``.  ``with_n`` defaults to
-    checking whether any 'N' is present.  Without N masks or per-pair
-    thresholds this is one ``shouji_pack_filter`` call.
+    Returns ``(accept_bool[n], count_uint8[n])``.  ``with_n=None`` (the
+    default) filters without N masks and runs again with them when the
+    device saw an 'N'.  Without N masks or per-pair thresholds this is one
+    ``shouji_pack_filter`` call.
     """
     n, m = reads.shape
     assert refs.shape == reads.shape
-    if with_n is None:
-        with_n = bool(((reads == 78).any() | (refs == 78).any()).item())
     if not with_n and E_per_pair is None:
+        if with_n is None:
+            shouji_unmasked_n()  # clear the flag
         _, _, acc, cnt = shouji_pack_filter(reads, refs, m, E, stream=stream)
-        return accept_to_bool(acc, n), cnt[:n]
-    pr, nr = shouji_pack(reads, m, with_n=with_n, stream=stream)
-    pt, nt = shouji_pack(refs, m, with_n=with_n, stream=stream)
+        if with_n is not None or not shouji_unmasked_n():
+            return accept_to_bool(acc, n), cnt[:n]
+        with_n = True
+    pr, nr, pt, nt = _pack_pairs(reads, refs, m, with_n, stream)
     acc, cnt, _ = shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
                                 E_per_pair=E_per_pair, stream=stream)
     return accept_to_bool(acc, n), cnt[:n]
@@ -371,10 +441,7 @@ def magnet_pairs(reads, refs, E: int, *, with_n: bool | None = None, E_per_pair=
     """
     n, m = reads.shape
     assert refs.shape == reads.shape
-    if with_n is None:
-        with_n = bool(((reads == 78).any() | (refs == 78).any()).item())
-    pr, nr = shouji_pack(reads, m, with_n=with_n, stream=stream)
-    pt, nt = shouji_pack(refs, m, with_n=with_n, stream=stream)
+    pr, nr, pt, nt = _pack_pairs(reads, refs, m, with_n, stream)
     acc, cnt, _ = shouji_magnet(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt,
                                 E_per_pair=E_per_pair, stream=stream)
     return accept_to_bool(acc, n), cnt[:n]
@@ -470,6 +537,21 @@ class Batch:
             _ptr(out_accept), _ptr(out_count), _stream(stream)), "shouji_batch_run")
         return out_accept, out_count
 
+    def run_at(self, reads, ref_text, ref_offsets, lens, E_per_pair, *, n_pairs=None,
+               stride=None, out_accept=None, out_count=None, count: bool = True, stream=None):
+        """Like ``run``, with pair i's reference segment read from the device
+        text ``ref_text`` at byte ``ref_offsets[i]`` (CUDA int64 tensor)."""
+        torch = _torch()
+        n, stride, out_accept, out_count = self._args(reads, None, lens, E_per_pair, n_pairs,
+                                                      stride, out_accept, out_count)
+        if out_count is None and count:
+            out_count = torch.empty(max(1, n), dtype=torch.uint8, device=reads.device)
+        _check(load_library().shouji_batch_run_at(
+            self._h, _ptr(reads), stride, _ptr(ref_text), _ptr(ref_offsets), _ptr(lens),
+            _ptr(E_per_pair), n, _ptr(out_accept), _ptr(out_count), _stream(stream)),
+            "shouji_batch_run_at")
+        return out_accept, out_count
+
     def tune(self, reads, refs, lens, E_per_pair, *, n_pairs=None, stride=None,
              cache: str | None = None, stream=None):
         n, stride, out_accept, _ = self._args(reads, refs, lens, E_per_pair, n_pairs, stride,
@@ -478,6 +560,18 @@ class Batch:
             self._h, _ptr(reads), _ptr(refs), stride, _ptr(lens), _ptr(E_per_pair), n,
             _ptr(out_accept), None, cache.encode() if cache else None, _stream(stream)),
             "shouji_batch_tune")
+
+    def timing(self) -> dict:
+        """Stage durations (ms) the last run's graph recorded: ``graph``,
+        ``bucketing``, ``pack``, ``filters``, ``finalize`` and ``filter_E``
+        ({E: ms} for the thresholds in range)."""
+        n = 5 + SHOUJI_MAX_E + 1
+        buf = (ctypes.c_float * n)()
+        _check(load_library().shouji_batch_timing(self._h, buf, n), "shouji_batch_timing")
+        v = list(buf)
+        return {"graph": v[0], "bucketing": v[1], "pack": v[2], "filters": v[3],
+                "finalize": v[4], "filter_E": {E: v[5 + E] for E in range(SHOUJI_MAX_E + 1)
+                                               if v[5 + E] >= 0}}
 
     def invalid(self) -> int:
         v = ctypes.c_uint64(0)
@@ -497,17 +591,39 @@ class Batch:
             pass
 
 
+class _ServerRequest(ctypes.Structure):
+    _fields_ = [("reads", ctypes.c_void_p), ("refs", ctypes.c_void_p),
+                ("stride", ctypes.c_uint64), ("ref_id", ctypes.c_uint32),
+                ("ref_offsets", ctypes.c_void_p), ("lens", ctypes.c_void_p),
+                ("E_per_pair", ctypes.c_void_p), ("n_pairs", ctypes.c_size_t),
+                ("accept", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("flags", ctypes.c_int)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("used_bytes", ctypes.c_uint64),
+                ("peak_used_bytes", ctypes.c_uint64), ("reference_bytes", ctypes.c_uint64),
+                ("workers", ctypes.c_int), ("busy_workers", ctypes.c_int),
+                ("peak_busy_workers", ctypes.c_int), ("queued", ctypes.c_int),
+                ("admitted", ctypes.c_uint64), ("workers_made", ctypes.c_uint64),
+                ("workers_released", ctypes.c_uint64)]
+
+
+SERVE_DEVICE_RESULTS = 1
+
+
 class Server:
     """``shouji_server_*``: requests of mixed lengths and thresholds filtered as
-    they arrive, with continuous batching over memory-budgeted slots.
+    they arrive, admitted by device memory (continuous batching).
 
-    Buffers are numpy arrays or CPU torch tensors (pinned for overlap) and must
-    stay alive until ``wait`` returns for the request.
+    Host buffers are numpy arrays or CPU torch tensors (pinned for overlap)
+    and must stay alive until ``wait`` returns for the request; with
+    ``device_results`` the outputs are CUDA tensors written on the device.
     """
 
     def __init__(self, max_request_pairs: int, max_m: int, e_min: int, e_max: int, *,
                  max_stride: int | None = None, with_n: bool = False,
-                 memory_budget: int = 40 << 30, max_slots: int = 8,
+                 memory_budget: int = 40 << 30, max_slots: int = 64,
                  tune_cache: str | None = None):
         lib = load_library()
         h = ctypes.c_void_p()
@@ -520,34 +636,75 @@ class Server:
         self._keep = {}
 
     def info(self):
+        """(workers held now, device bytes of a worker for the largest request)."""
         slots = ctypes.c_int(0)
         bps = ctypes.c_uint64(0)
         _check(load_library().shouji_server_info(self._h, ctypes.byref(slots), ctypes.byref(bps)),
                "shouji_server_info")
         return slots.value, bps.value
 
-    def submit(self, reads, refs, lens, E_per_pair, accept, count=None, *, n_pairs=None,
-               stride=None) -> int:
-        n = len(lens) if n_pairs is None else n_pairs
-        stride = reads.shape[1] if stride is None else stride
-        rid = ctypes.c_uint64(0)
-        _check(load_library().shouji_server_submit(
-            self._h, _host_ptr(reads), _host_ptr(refs), stride, _host_ptr(lens),
-            _host_ptr(E_per_pair), n, _host_ptr(accept), _host_ptr(count), ctypes.byref(rid)),
-            "shouji_server_submit")
-        self._keep[rid.value] = (reads, refs, lens, E_per_pair, accept, count)
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(load_library().shouji_server_stats_read(self._h, ctypes.byref(st)),
+               "shouji_server_stats_read")
+        return {name: getattr(st, name) for name, _ in _ServerStats._fields_}
+
+    def add_reference(self, text) -> int:
+        """Make a reference text (host bytes) resident on the device; its id."""
+        rid = ctypes.c_uint32(0)
+        _check(load_library().shouji_server_add_reference(
+            self._h, _host_ptr(text), int(text.nbytes if hasattr(text, "nbytes") else len(text)),
+            ctypes.byref(rid)), "shouji_server_add_reference")
         return rid.value
 
-    def wait(self, request_id: int, timeout: float = 60.0) -> float:
-        """Block until done; returns the latency in seconds.  Raises
-        ``ShoujiError`` with status 4 (SHOUJI_ETIMEOUT) when the deadline passes."""
-        lat = ctypes.c_double(0.0)
-        st = load_library().shouji_server_wait(self._h, request_id, float(timeout),
-                                               ctypes.byref(lat))
+    def _submit(self, req, keep) -> int:
+        rid = ctypes.c_uint64(0)
+        _check(load_library().shouji_server_submit_request(self._h, ctypes.byref(req),
+                                                           ctypes.byref(rid)),
+               "shouji_server_submit_request")
+        self._keep[rid.value] = keep
+        return rid.value
+
+    def _outs(self, accept, count, device_results):
+        if device_results:
+            return _ptr(accept), _ptr(count), SERVE_DEVICE_RESULTS
+        return _host_ptr(accept), _host_ptr(count), 0
+
+    def submit(self, reads, refs, lens, E_per_pair, accept, count=None, *, n_pairs=None,
+               stride=None, device_results: bool = False) -> int:
+        """Pairs given as host rows of reads and reference segments."""
+        n = len(lens) if n_pairs is None else n_pairs
+        stride = reads.shape[1] if stride is None else stride
+        acc, cnt, flags = self._outs(accept, count, device_results)
+        req = _ServerRequest(_host_ptr(reads), _host_ptr(refs), stride, 0, None,
+                             _host_ptr(lens), _host_ptr(E_per_pair), n, acc, cnt, flags)
+        return self._submit(req, (reads, refs, lens, E_per_pair, accept, count))
+
+    def submit_at(self, reads, ref_id: int, ref_offsets, lens, E_per_pair, accept, count=None,
+                  *, n_pairs=None, stride=None, device_results: bool = False) -> int:
+        """Pairs given as host rows of reads and offsets (host uint64) of
+        their reference segments in the resident text ``ref_id``."""
+        n = len(lens) if n_pairs is None else n_pairs
+        stride = reads.shape[1] if stride is None else stride
+        acc, cnt, flags = self._outs(accept, count, device_results)
+        req = _ServerRequest(_host_ptr(reads), None, stride, ref_id, _host_ptr(ref_offsets),
+                             _host_ptr(lens), _host_ptr(E_per_pair), n, acc, cnt, flags)
+        return self._submit(req, (reads, ref_offsets, lens, E_per_pair, accept, count))
+
+    def wait_timed(self, request_id: int, timeout: float = 60.0):
+        """Block until done; returns (latency, gpu_start, gpu_end) in seconds
+        (GPU times since the server was created).  Raises ``ShoujiError`` with
+        status 4 (SHOUJI_ETIMEOUT) when the deadline passes."""
+        t = (ctypes.c_double * 3)(-1.0, -1.0, -1.0)
+        st = load_library().shouji_server_wait_timed(self._h, request_id, float(timeout), t)
         if st != 4:
             self._keep.pop(request_id, None)
-        _check(st, "shouji_server_wait")
-        return lat.value
+        _check(st, "shouji_server_wait_timed")
+        return t[0], t[1], t[2]
+
+    def wait(self, request_id: int, timeout: float = 60.0) -> float:
+        """Block until done; returns the latency in seconds."""
+        return self.wait_timed(request_id, timeout)[0]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

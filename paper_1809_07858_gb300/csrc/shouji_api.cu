@@ -14,6 +14,21 @@ shouji_status cuda_status(cudaError_t e)
     return SHOUJI_ECUDA;
 }
 
+cudaError_t take_unmasked_n(uint32_t *seen)
+{
+    *seen = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    uint32_t a = 0, b = 0, c = 0;
+    if (e == cudaSuccess)
+        e = take_pack_unmasked_n(&a);
+    if (e == cudaSuccess)
+        e = take_fused_unmasked_n(&b);
+    if (e == cudaSuccess)
+        e = take_batch_unmasked_n(&c);
+    *seen = a | b | c;
+    return e;
+}
+
 namespace {
 
 using LaunchFn = cudaError_t (*)(const FilterArgs &, cudaStream_t);
@@ -87,6 +102,25 @@ shouji_status shouji_selftest_pack_wait(uint32_t *failures)
     return cuda_status(selftest_pack_wait(failures));
 }
 
+shouji_status shouji_unmasked_n(int *seen)
+{
+    if (!seen)
+        return SHOUJI_EINVAL;
+    uint32_t v = 0;
+    const cudaError_t e = take_unmasked_n(&v);
+    *seen = v ? 1 : 0;
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    return v ? SHOUJI_EINVAL : SHOUJI_OK;
+}
+
+shouji_status shouji_alu_probe(int op, double *lane_ops_per_sm_clock)
+{
+    if (!lane_ops_per_sm_clock || op < SHOUJI_PROBE_LOP3 || op > SHOUJI_PROBE_LOP3_IMAD)
+        return SHOUJI_EINVAL;
+    return cuda_status(alu_probe(op, lane_ops_per_sm_clock));
+}
+
 shouji_status shouji_filter(const uint32_t *reads, const uint32_t *refs,
                             const uint32_t *reads_nmask, const uint32_t *refs_nmask,
                             uint32_t m, size_t n_pairs, int E, const uint8_t *E_per_pair,
@@ -154,6 +188,22 @@ shouji_status shouji_pack_filter(const uint8_t *reads, const uint8_t *refs, uint
     a.n_pairs = n_pairs;
     a.m = (int)m;
     return cuda_status(launch_filter(a, E, s));
+}
+
+shouji_status shouji_pack_filter_fused(const uint8_t *reads, const uint8_t *refs,
+                                       uint64_t stride, uint32_t m, int E, int *fused)
+{
+    if (!fused)
+        return SHOUJI_EINVAL;
+    *fused = 0;
+    if (m < 1 || m > SHOUJI_MAX_M || stride < m || E < 0 || E > SHOUJI_MAX_E)
+        return SHOUJI_EINVAL;
+    if (stride != m || (uintptr_t)reads % 16 || (uintptr_t)refs % 16 || !reads || !refs)
+        return SHOUJI_OK;
+    bool applies = false;
+    const shouji_status st = cuda_status(pack_filter_kernel_applies((int)m, E, &applies));
+    *fused = applies ? 1 : 0;
+    return st;
 }
 
 size_t shouji_compact_workspace_size(size_t n_pairs)

@@ -35,6 +35,9 @@ namespace shouji {
 namespace batch {
 namespace {
 
+// Set when a batch without N masks read an 'N' (see shouji_unmasked_n).
+__device__ unsigned int g_batch_unmasked_n;
+
 constexpr int kClsThreads = 256;
 constexpr int kClsItems = 16;                       // pairs per thread
 constexpr int kClsPairs = kClsThreads * kClsItems;  // pairs per CTA
@@ -232,8 +235,9 @@ pack_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int max_m,
     uint8_t *sb = reinterpret_cast<uint8_t *>(sm);
     const uint8_t *seqs = blockIdx.y ? a->refs : a->reads;
     const uint64_t stride = a->stride;
+    const uint64_t *off = blockIdx.y ? a->ref_off : nullptr;  // rows at offsets
     // rows on 16-byte boundaries are packed by pack_async_kernel instead
-    if (rows_on_16_bytes(seqs, stride, max_m))
+    if (!off && rows_on_16_bytes(seqs, stride, max_m))
         return;
     const uint32_t nmc = T->n_mc;
     if (nmc == 0)
@@ -267,8 +271,9 @@ pack_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int max_m,
                 uint8_t v[8][8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const uint8_t *src = seqs + (uint64_t)(pair[k] == kNoPair ? 0 : pair[k]) * stride;
                     const bool ok = pair[k] != kNoPair;
+                    const uint64_t p = ok ? pair[k] : 0;
+                    const uint8_t *src = seqs + (off ? (ok ? off[p] : 0) : p * stride);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int j = ln + 32 * q;
@@ -293,9 +298,13 @@ pack_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int max_m,
         const int lane0 = (int)((rel % kTile) / 32);
         uint32_t *packed = reinterpret_cast<uint32_t *>((blockIdx.y ? prefs : preads) + T->mc_poff[lo]);
         uint32_t *nmask = WITH_N ? (blockIdx.y ? nrefs : nreads) + T->mc_poff[lo] : nullptr;
-        packdev::pack_transpose<WITH_N, true, kPackLanes>(
+        const uint32_t seen = packdev::pack_transpose<WITH_N, true, kPackLanes>(
             sm, m, rs, tile, lane0, packed, nmask, packdev::rotation_step(rs, kPackLanes), kPackThreads);
-        __syncthreads();  // sm is refilled for the next block
+        // sm is refilled for the next block after this barrier
+        if (WITH_N)
+            __syncthreads();
+        else if (__syncthreads_or(packdev::has_n_bytes(seen)) && threadIdx.x == 0)
+            g_batch_unmasked_n = 1u;
     }
 }
 
@@ -357,7 +366,7 @@ pack_async_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int 
     __shared__ uint32_t P[3][kPackSeqs];   // permutation entries of three blocks
     const uint8_t *seqs = blockIdx.y ? a->refs : a->reads;
     const uint64_t stride = a->stride;
-    if (!rows_on_16_bytes(seqs, stride, max_m))
+    if (!rows_on_16_bytes(seqs, stride, max_m) || (blockIdx.y && a->ref_off))
         return;  // pack_kernel does this side
     if (threadIdx.x == 0) {
         mc.n_mc = T->n_mc;
@@ -417,11 +426,15 @@ pack_async_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int 
         const int lane0 = (int)((b.rel % kTile) / 32);
         uint32_t *packed = reinterpret_cast<uint32_t *>((blockIdx.y ? prefs : preads) + mc.poff[b.mc]);
         uint32_t *nmask = WITH_N ? (blockIdx.y ? nrefs : nreads) + mc.poff[b.mc] : nullptr;
-        packdev::pack_transpose<WITH_N, true, kPackLanes>(
+        const uint32_t seen = packdev::pack_transpose<WITH_N, true, kPackLanes>(
             reinterpret_cast<const uint32_t *>((k & 1) ? buf1 : buf0), b.m, b.rs, tile, lane0,
             packed, nmask, packdev::rotation_step(b.rs, kPackLanes), kPackThreads);
         P[(k + 2) % 3][threadIdx.x] = ahead;
-        __syncthreads();  // the buffer of block k is refilled in step k+1
+        // the buffer of block k is refilled in step k+1, after this barrier
+        if (WITH_N)
+            __syncthreads();
+        else if (__syncthreads_or(packdev::has_n_bytes(seen)) && threadIdx.x == 0)
+            g_batch_unmasked_n = 1u;
     }
     cp_async_wait<0>();
 }
@@ -454,10 +467,26 @@ finalize_kernel(const Args *__restrict__ a, const Tables *__restrict__ T,
 
 }  // namespace
 }  // namespace batch
+
+cudaError_t take_batch_unmasked_n(uint32_t *seen)
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, batch::g_batch_unmasked_n, sizeof v);
+    if (e == cudaSuccess && v) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(batch::g_batch_unmasked_n, &zero, sizeof zero);
+    }
+    *seen = v;
+    return e;
+}
+
 }  // namespace shouji
 
 using namespace shouji;
 using namespace shouji::batch;
+
+// Argument blocks (and captured graphs) a batch object cycles through.
+constexpr int kArgBufs = 2;
 
 struct shouji_batch {
     int device = 0;
@@ -470,7 +499,8 @@ struct shouji_batch {
     int pack_grid = 0;      // CTAs per side of the fallback pack (walks the blocks)
     int async_grid = 0;     // CTAs per side of the persistent pack (0: not used)
     int async_buf = 0;      // bytes of one shared-memory buffer
-    Args *d_args = nullptr, *h_args = nullptr;
+    Args *d_args = nullptr;
+    Args *h_args = nullptr;          // kArgBufs pinned argument blocks
     uint32_t *d_hist = nullptr;
     Tables *d_tables = nullptr;
     uint16_t *d_keys = nullptr;
@@ -479,16 +509,31 @@ struct shouji_batch {
     uint2 *d_pr = nullptr, *d_pt = nullptr;
     uint32_t *d_nr = nullptr, *d_nt = nullptr;
     int threads[kMaxE], ctas_per_sm[kMaxE], schedule[kMaxE];
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t done = nullptr;
+    // One graph per argument block: graph k copies block k, so a run waits
+    // only for the run kArgBufs runs before it to have started.
+    cudaGraph_t graph[kArgBufs] = {};
+    cudaGraphExec_t exec[kArgBufs] = {};
+    cudaEvent_t done[kArgBufs] = {};
+    bool launched[kArgBufs] = {};
+    int next = 0;                    // argument block of the next run
+    int last = -1;                   // argument block of the last run
     cudaStream_t capture = nullptr;  // private stream the graph is captured on
     cudaStream_t aux[kMaxE] = {};    // graph branches: one per threshold
     cudaEvent_t fork = nullptr, join[kMaxE] = {};
-    bool launched = false;
+    // Timing events recorded by the graph itself (shouji_batch_timing).
+    cudaEvent_t t_begin = nullptr, t_bucketed = nullptr, t_packed = nullptr,
+                t_joined = nullptr, t_end = nullptr;
+    cudaEvent_t t_e0[kMaxE] = {}, t_e1[kMaxE] = {};
 };
 
 namespace {
+
+// An event record that becomes a node of the graph being captured, so its
+// time stamp is taken every time the graph runs.
+cudaError_t stamp(cudaEvent_t ev, cudaStream_t s)
+{
+    return ev ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaSuccess;
+}
 
 using BatchLaunch = cudaError_t (*)(const FilterParams &, int, int, cudaStream_t);
 constexpr BatchLaunch kBatchFilter[kMaxE] = {
@@ -542,11 +587,14 @@ FilterParams filter_params(const shouji_batch *b)
     return p;
 }
 
-// The stages before the per-threshold filters.
-cudaError_t enqueue_prologue(shouji_batch *b, cudaStream_t s)
+// The stages before the per-threshold filters, with argument block k.
+// `timed`: record the graph's timing events (only inside a capture).
+cudaError_t enqueue_prologue(shouji_batch *b, cudaStream_t s, int k, bool timed)
 {
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(b->d_args, b->h_args, sizeof(Args), cudaMemcpyHostToDevice, s)))
+    if (timed && (e = stamp(b->t_begin, s)))
+        return e;
+    if ((e = cudaMemcpyAsync(b->d_args, b->h_args + k, sizeof(Args), cudaMemcpyHostToDevice, s)))
         return e;
     if ((e = cudaMemsetAsync(b->d_hist, 0, sizeof(uint32_t) * kBins, s)))
         return e;
@@ -561,6 +609,8 @@ cudaError_t enqueue_prologue(shouji_batch *b, cudaStream_t s)
     fill_kernel<<<b->sms * 4, 256, 0, s>>>(b->d_tables, b->d_perm);
     scatter_kernel<<<b->sms * 8, 256, 0, s>>>(b->d_args, b->d_tables, b->d_keys, b->d_ranks,
                                               b->d_perm);
+    if (timed && (e = stamp(b->t_bucketed, s)))
+        return e;
     // The persistent double-buffered pack needs rows on 16-byte boundaries;
     // the stride is known only per run, so both forms are in the graph and
     // each exits at once when the other one applies.
@@ -579,7 +629,9 @@ cudaError_t enqueue_prologue(shouji_batch *b, cudaStream_t s)
             b->d_args, b->d_tables, (int)b->max_m, b->async_buf, b->d_perm, b->d_pr, b->d_pt,
             nullptr, nullptr);
     }
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()))
+        return e;
+    return timed ? stamp(b->t_packed, s) : cudaSuccess;
 }
 
 cudaError_t enqueue_filter(shouji_batch *b, int E, int threads, int ctas_per_sm, int schedule,
@@ -593,9 +645,9 @@ cudaError_t enqueue_filter(shouji_batch *b, int E, int threads, int ctas_per_sm,
 // The threshold kernels are independent: in the graph they are parallel
 // branches (fork after the pack, join before the finalize), so batches whose
 // thresholds each hold little work still fill the GPU.
-cudaError_t enqueue_all(shouji_batch *b, cudaStream_t s)
+cudaError_t enqueue_all(shouji_batch *b, cudaStream_t s, int k)
 {
-    cudaError_t e = enqueue_prologue(b, s);
+    cudaError_t e = enqueue_prologue(b, s, k, true);
     if (e)
         return e;
     if ((e = cudaEventRecord(b->fork, s)))
@@ -604,42 +656,56 @@ cudaError_t enqueue_all(shouji_batch *b, cudaStream_t s)
         cudaStream_t t = b->aux[E];
         if ((e = cudaStreamWaitEvent(t, b->fork, 0)))
             return e;
+        if ((e = stamp(b->t_e0[E], t)))
+            return e;
         if ((e = enqueue_filter(b, E, b->threads[E], b->ctas_per_sm[E], b->schedule[E], t)))
+            return e;
+        if ((e = stamp(b->t_e1[E], t)))
             return e;
         if ((e = cudaEventRecord(b->join[E], t)))
             return e;
         if ((e = cudaStreamWaitEvent(s, b->join[E], 0)))
             return e;
     }
+    if ((e = stamp(b->t_joined, s)))
+        return e;
     const unsigned fin_blocks = (unsigned)((b->max_pairs + 255) / 256);
     finalize_kernel<<<fin_blocks ? fin_blocks : 1, 256, 0, s>>>(b->d_args, b->d_tables, b->d_keys,
                                                                 b->d_ranks, b->d_count_slot);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()))
+        return e;
+    return stamp(b->t_end, s);
 }
 
-void drop_graph(shouji_batch *b)
+// Waits for every run still in flight, then drops the graphs.
+void drop_graphs(shouji_batch *b)
 {
-    if (b->exec)
-        cudaGraphExecDestroy(b->exec);
-    if (b->graph)
-        cudaGraphDestroy(b->graph);
-    b->exec = nullptr;
-    b->graph = nullptr;
+    for (int k = 0; k < kArgBufs; ++k) {
+        if (b->launched[k])
+            cudaEventSynchronize(b->done[k]);
+        b->launched[k] = false;
+        if (b->exec[k])
+            cudaGraphExecDestroy(b->exec[k]);
+        if (b->graph[k])
+            cudaGraphDestroy(b->graph[k]);
+        b->exec[k] = nullptr;
+        b->graph[k] = nullptr;
+    }
+    b->last = -1;
 }
 
-cudaError_t build_graph(shouji_batch *b, cudaStream_t s)
+cudaError_t build_graph(shouji_batch *b, cudaStream_t s, int k)
 {
-    drop_graph(b);
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e)
         return e;
-    cudaError_t e2 = enqueue_all(b, s);
-    e = cudaStreamEndCapture(s, &b->graph);
+    cudaError_t e2 = enqueue_all(b, s, k);
+    e = cudaStreamEndCapture(s, &b->graph[k]);
     if (e2)
         return e2;
     if (e)
         return e;
-    return cudaGraphInstantiate(&b->exec, b->graph, 0);
+    return cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
 }
 
 void release(shouji_batch *b)
@@ -647,11 +713,19 @@ void release(shouji_batch *b)
     if (!b)
         return;
     DeviceGuard g(b->device);
-    if (b->done) {
-        cudaEventSynchronize(b->done);
-        cudaEventDestroy(b->done);
+    drop_graphs(b);
+    for (int k = 0; k < kArgBufs; ++k)
+        if (b->done[k])
+            cudaEventDestroy(b->done[k]);
+    for (cudaEvent_t ev : {b->t_begin, b->t_bucketed, b->t_packed, b->t_joined, b->t_end})
+        if (ev)
+            cudaEventDestroy(ev);
+    for (int E = 0; E < kMaxE; ++E) {
+        if (b->t_e0[E])
+            cudaEventDestroy(b->t_e0[E]);
+        if (b->t_e1[E])
+            cudaEventDestroy(b->t_e1[E]);
     }
-    drop_graph(b);
     if (b->capture)
         cudaStreamDestroy(b->capture);
     for (int E = 0; E < kMaxE; ++E) {
@@ -691,6 +765,30 @@ void device_name(char *out, size_t cap, int dev)
             *c = '_';
 }
 
+// Slots a batch of up to n pairs can occupy: every non-empty bucket pads to
+// 32 slots and every non-empty m-class to a 1024-slot tile, and there are at
+// most min(n, lengths x thresholds) buckets and min(n, lengths) m-classes.
+size_t slots_capacity(size_t n, uint32_t max_m, int e_min, int e_max)
+{
+    const size_t buckets = (size_t)max_m * (size_t)(e_max - e_min + 1);
+    const size_t classes = max_m;
+    const size_t s = n + 31 * (n < buckets ? n : buckets) + (kTile - 1) * (n < classes ? n : classes);
+    return (s + kTile - 1) / kTile * kTile;
+}
+
+// Device bytes shouji_batch_create allocates (its cudaMalloc calls, in order).
+size_t batch_bytes(size_t max_pairs, uint32_t max_m, int e_min, int e_max, int with_n)
+{
+    const size_t slots = slots_capacity(max_pairs, max_m, e_min, e_max);
+    const size_t packed_u2 = slots / kTile * max_m * kLanes;
+    size_t b = sizeof(Args) + sizeof(uint32_t) * kBins + sizeof(Tables) +
+               sizeof(uint16_t) * max_pairs + sizeof(uint32_t) * max_pairs +
+               sizeof(uint32_t) * slots + slots + 2 * sizeof(uint2) * packed_u2;
+    if (with_n)
+        b += 2 * sizeof(uint32_t) * packed_u2;
+    return b;
+}
+
 // Tuning cache: lines "<gpu> <E> <threads> <ctas_per_sm> <schedule> <ms>".
 void load_cache(shouji_batch *b, const char *path)
 {
@@ -714,20 +812,23 @@ void load_cache(shouji_batch *b, const char *path)
     fclose(f);
 }
 
-shouji_status set_args(shouji_batch *b, const uint8_t *reads, const uint8_t *refs,
+// Writes argument block k (that of the next run).
+shouji_status set_args(shouji_batch *b, int k, const uint8_t *reads, const uint8_t *refs,
                        uint64_t stride, const uint16_t *lens, const uint8_t *E_per_pair,
-                       size_t n, uint32_t *accept, uint8_t *count)
+                       size_t n, uint32_t *accept, uint8_t *count,
+                       const uint64_t *ref_off = nullptr)
 {
-    if (b->launched) {
-        // the previous launch must have copied its argument block
-        cudaError_t e = cudaEventSynchronize(b->done);
+    if (b->launched[k]) {
+        // the run that last used block k must have copied it
+        cudaError_t e = cudaEventSynchronize(b->done[k]);
         if (e)
             return cuda_status(e);
     }
-    Args *a = b->h_args;
+    Args *a = b->h_args + k;
     a->reads = reads;
     a->refs = refs;
     a->stride = stride;
+    a->ref_off = ref_off;
     a->lens = lens;
     a->E_per_pair = E_per_pair;
     a->n = n;
@@ -739,6 +840,15 @@ shouji_status set_args(shouji_batch *b, const uint8_t *reads, const uint8_t *ref
 }  // namespace
 
 extern "C" {
+
+size_t shouji_batch_device_bytes(size_t max_pairs, uint32_t max_m, int e_min, int e_max,
+                                 int with_n)
+{
+    if (max_pairs == 0 || max_m < 1 || max_m > SHOUJI_MAX_M || e_min < 0 || e_max > SHOUJI_MAX_E ||
+        e_min > e_max)
+        return 0;
+    return batch_bytes(max_pairs, max_m, e_min, e_max, with_n);
+}
 
 shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, int e_max,
                                   int with_n, const char *tune_cache, shouji_batch **out)
@@ -767,9 +877,7 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, i
         b->ctas_per_sm[E] = 4;
         b->schedule[E] = 0;
     }
-    // every bucket pads to 32 slots and every m-class to 1024
-    b->slots_cap = (max_pairs + (size_t)kBins * 31 + (size_t)(kMaxM - 1) * (kTile - 1) + kTile - 1) /
-                   kTile * kTile;
+    b->slots_cap = slots_capacity(max_pairs, max_m, e_min, e_max);
     b->pack_blocks_cap = b->slots_cap / kPackSeqs;
     b->pack_grid = (int)(b->pack_blocks_cap < (size_t)b->sms * 8 ? b->pack_blocks_cap
                                                                   : (size_t)b->sms * 8);
@@ -778,7 +886,7 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, i
     const size_t packed_u2 = b->slots_cap / kTile * max_m * kLanes;  // uint2 per side
     bool ok = true;
     ok = ok && cudaMalloc(&b->d_args, sizeof(Args)) == cudaSuccess;
-    ok = ok && cudaMallocHost(&b->h_args, sizeof(Args)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&b->h_args, kArgBufs * sizeof(Args)) == cudaSuccess;
     ok = ok && cudaMalloc(&b->d_hist, sizeof(uint32_t) * kBins) == cudaSuccess;
     ok = ok && cudaMalloc(&b->d_tables, sizeof(Tables)) == cudaSuccess;
     ok = ok && cudaMalloc(&b->d_keys, sizeof(uint16_t) * max_pairs) == cudaSuccess;
@@ -791,7 +899,12 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, i
         ok = ok && cudaMalloc(&b->d_nr, sizeof(uint32_t) * packed_u2) == cudaSuccess;
         ok = ok && cudaMalloc(&b->d_nt, sizeof(uint32_t) * packed_u2) == cudaSuccess;
     }
-    ok = ok && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kArgBufs; ++k)
+        ok = ok && cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming) == cudaSuccess;
+    for (cudaEvent_t *ev : {&b->t_begin, &b->t_bucketed, &b->t_packed, &b->t_joined, &b->t_end})
+        ok = ok && cudaEventCreate(ev) == cudaSuccess;
+    for (int E = e_min; E <= e_max && ok; ++E)
+        ok = cudaEventCreate(&b->t_e0[E]) == cudaSuccess && cudaEventCreate(&b->t_e1[E]) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
     for (int E = e_min; E <= e_max && ok; ++E) {
@@ -834,7 +947,7 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, i
         release(b);
         return SHOUJI_ENOMEM;
     }
-    memset(b->h_args, 0, sizeof(Args));
+    memset(b->h_args, 0, kArgBufs * sizeof(Args));
     load_cache(b, tune_cache);
     *out = b;
     return SHOUJI_OK;
@@ -842,10 +955,14 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, i
 
 void shouji_batch_destroy(shouji_batch *b) { release(b); }
 
-shouji_status shouji_batch_run(shouji_batch *b, const uint8_t *reads, const uint8_t *refs,
-                               uint64_t stride, const uint16_t *lens, const uint8_t *E_per_pair,
-                               size_t n_pairs, uint32_t *out_accept, uint8_t *out_count,
-                               void *stream)
+}  // extern "C"
+
+namespace {
+
+shouji_status batch_run(shouji_batch *b, const uint8_t *reads, const uint8_t *refs,
+                        uint64_t stride, const uint64_t *ref_off, const uint16_t *lens,
+                        const uint8_t *E_per_pair, size_t n_pairs, uint32_t *out_accept,
+                        uint8_t *out_count, void *stream)
 {
     if (!b || n_pairs > b->max_pairs || stride < 1)
         return SHOUJI_EINVAL;
@@ -855,21 +972,74 @@ shouji_status shouji_batch_run(shouji_batch *b, const uint8_t *reads, const uint
         return SHOUJI_EINVAL;
     DeviceGuard g(b->device);
     cudaStream_t s = (cudaStream_t)stream;
-    shouji_status st = set_args(b, reads, refs, stride, lens, E_per_pair, n_pairs, out_accept,
-                                out_count);
+    const int k = b->next;
+    shouji_status st = set_args(b, k, reads, refs, stride, lens, E_per_pair, n_pairs, out_accept,
+                                out_count, ref_off);
     if (st)
         return st;
     cudaError_t e = cudaSuccess;
-    // The graph is captured on the object's own stream (the caller's may be
+    // The graphs are captured on the object's own stream (the caller's may be
     // the legacy default stream, which cannot be captured) and launched on
     // the caller's.
-    if (!b->exec && (e = build_graph(b, b->capture)))
+    if (!b->exec[k] && (e = build_graph(b, b->capture, k)))
         return cuda_status(e);
-    if ((e = cudaGraphLaunch(b->exec, s)))
+    if ((e = cudaGraphLaunch(b->exec[k], s)))
         return cuda_status(e);
-    if ((e = cudaEventRecord(b->done, s)))
+    if ((e = cudaEventRecord(b->done[k], s)))
         return cuda_status(e);
-    b->launched = true;
+    b->launched[k] = true;
+    b->last = k;
+    b->next = (k + 1) % kArgBufs;
+    return SHOUJI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+shouji_status shouji_batch_run(shouji_batch *b, const uint8_t *reads, const uint8_t *refs,
+                               uint64_t stride, const uint16_t *lens, const uint8_t *E_per_pair,
+                               size_t n_pairs, uint32_t *out_accept, uint8_t *out_count,
+                               void *stream)
+{
+    return batch_run(b, reads, refs, stride, nullptr, lens, E_per_pair, n_pairs, out_accept,
+                     out_count, stream);
+}
+
+shouji_status shouji_batch_run_at(shouji_batch *b, const uint8_t *reads, uint64_t stride,
+                                  const uint8_t *ref_text, const uint64_t *ref_offsets,
+                                  const uint16_t *lens, const uint8_t *E_per_pair,
+                                  size_t n_pairs, uint32_t *out_accept, uint8_t *out_count,
+                                  void *stream)
+{
+    if (!ref_offsets && n_pairs)
+        return SHOUJI_EINVAL;
+    return batch_run(b, reads, ref_text, stride, ref_offsets, lens, E_per_pair, n_pairs,
+                     out_accept, out_count, stream);
+}
+
+shouji_status shouji_batch_timing(shouji_batch *b, float *ms, int n)
+{
+    if (!b || !ms || n < SHOUJI_BATCH_TIMES)
+        return SHOUJI_EINVAL;
+    for (int i = 0; i < SHOUJI_BATCH_TIMES; ++i)
+        ms[i] = -1.f;
+    if (b->last < 0)
+        return SHOUJI_OK;
+    DeviceGuard g(b->device);
+    cudaError_t e = cudaEventSynchronize(b->done[b->last]);
+    if (e)
+        return cuda_status(e);
+    auto span = [&](cudaEvent_t a, cudaEvent_t z, float *out) -> cudaError_t {
+        return cudaEventElapsedTime(out, a, z);
+    };
+    if ((e = span(b->t_begin, b->t_end, &ms[0])) || (e = span(b->t_begin, b->t_bucketed, &ms[1])) ||
+        (e = span(b->t_bucketed, b->t_packed, &ms[2])) ||
+        (e = span(b->t_packed, b->t_joined, &ms[3])) || (e = span(b->t_joined, b->t_end, &ms[4])))
+        return cuda_status(e);
+    for (int E = b->e_lo; E <= b->e_hi; ++E)
+        if ((e = span(b->t_e0[E], b->t_e1[E], &ms[5 + E])))
+            return cuda_status(e);
     return SHOUJI_OK;
 }
 
@@ -878,13 +1048,13 @@ shouji_status shouji_batch_invalid(shouji_batch *b, uint64_t *n_invalid)
     if (!b || !n_invalid)
         return SHOUJI_EINVAL;
     DeviceGuard g(b->device);
-    cudaError_t e = b->launched ? cudaEventSynchronize(b->done) : cudaSuccess;
+    cudaError_t e = b->last >= 0 ? cudaEventSynchronize(b->done[b->last]) : cudaSuccess;
     uint32_t v = 0;
     if (!e)
         e = cudaMemcpy(&v, &b->d_tables->n_invalid, sizeof(v), cudaMemcpyDeviceToHost);
     if (e)
         return cuda_status(e);
-    *n_invalid = b->launched ? v : 0;
+    *n_invalid = b->last >= 0 ? v : 0;
     return SHOUJI_OK;
 }
 
@@ -898,11 +1068,12 @@ shouji_status shouji_batch_tune(shouji_batch *b, const uint8_t *reads, const uin
         return SHOUJI_EINVAL;
     DeviceGuard g(b->device);
     cudaStream_t s = (cudaStream_t)stream;
-    shouji_status st = set_args(b, reads, refs, stride, lens, E_per_pair, n_pairs, out_accept,
+    drop_graphs(b);  // waits for the runs in flight; re-captured after tuning
+    shouji_status st = set_args(b, 0, reads, refs, stride, lens, E_per_pair, n_pairs, out_accept,
                                 out_count);
     if (st)
         return st;
-    cudaError_t e = enqueue_prologue(b, s);
+    cudaError_t e = enqueue_prologue(b, s, 0, false);
     if (!e)
         e = cudaStreamSynchronize(s);
     if (e)
@@ -976,8 +1147,7 @@ shouji_status shouji_batch_tune(shouji_batch *b, const uint8_t *reads, const uin
     cudaEventDestroy(t1);
     if (e)
         return cuda_status(e);
-    drop_graph(b);  // re-captured with the tuned shapes on the next run
-    b->launched = false;
+    drop_graphs(b);  // re-captured with the tuned shapes on the next run
     return SHOUJI_OK;
 }
 

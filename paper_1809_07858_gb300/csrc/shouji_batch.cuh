@@ -27,6 +27,9 @@ constexpr uint32_t kNoPair = 0xFFFFFFFFu;
 struct Args {
     const uint8_t *reads, *refs;
     uint64_t stride;
+    // null: the reference of pair i is the row refs + i * stride; else it
+    // starts at refs + ref_off[i] (a reference text kept on the device)
+    const uint64_t *ref_off;
     const uint16_t *lens;
     const uint8_t *E_per_pair;
     uint64_t n;

@@ -11,42 +11,95 @@
 // file-scope __device__ array of fixed size instead.
 //
 // The array is a host-side stand-in in host code, not a device address, so
-// the host never passes it to a kernel directly: once per device, with that
-// device current, the first call asks cudaGetSymbolAddress for the device
-// address and caches it.  The array lives on every GPU that loads the
-// library until the process exits.
-#include <atomic>
+// the host never passes it to a kernel directly.  Its device address belongs
+// to a CUDA context (the module holding the array is loaded once per
+// context), not to a device: after cudaDeviceReset the device gets a new
+// primary context, and a program may also make its own driver-API context
+// current on the same GPU.  So the address is looked up with
+// cudaGetSymbolAddress once per context, with that context current, and
+// cached under the context's unique id (cuCtxGetId; ids are never reused
+// within a process).  A call in a context not seen before looks the address
+// up again.  The array lives on every GPU, in every context, that has used
+// this entry point, until that context is destroyed.
+#include <mutex>
 
 #include "shouji_internal.cuh"
 
 namespace shouji {
 namespace {
 
-constexpr int kNoallocMaxDevices = 64;
 // 64 KB: one uint32 per slice of 32 * kCompactSliceWords pairs, up to
 // SHOUJI_NOALLOC_MAX_PAIRS pairs.
 constexpr size_t kNoallocMaxSlices = SHOUJI_NOALLOC_MAX_PAIRS / (32 * (size_t)kCompactSliceWords);
 
 static __device__ __align__(256) uint32_t g_compact_scratch[kNoallocMaxSlices];
 
-std::atomic<void *> g_scratch_addr[kNoallocMaxDevices];
+// Driver entry points, taken through the runtime so that the library needs
+// no link against the driver library.
+using CtxGetCurrentFn = int (*)(void **ctx);
+using CtxGetIdFn = int (*)(void *ctx, unsigned long long *id);
 
-// Device address of g_compact_scratch on the current device (set-up on the
-// first call per device).
+struct ScratchCache {
+    std::mutex mu;
+    CtxGetCurrentFn get_current = nullptr;
+    CtxGetIdFn get_id = nullptr;
+    bool resolved = false;
+    static constexpr int kSlots = 64;
+    unsigned long long ids[kSlots] = {};  // 0 = empty (context ids start at 1)
+    void *addr[kSlots] = {};
+    int next = 0;                         // slot replaced when all are taken
+};
+ScratchCache g_cache;
+
+// Unique id of the context current on this thread (0 when none or when the
+// driver entry points are missing).
+unsigned long long current_context_id()
+{
+    if (!g_cache.resolved) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_cache.get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_cache.get_id = reinterpret_cast<CtxGetIdFn>(f);
+        g_cache.resolved = true;
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!g_cache.get_current || !g_cache.get_id || g_cache.get_current(&ctx) != 0 || !ctx ||
+        g_cache.get_id(ctx, &id) != 0)
+        return 0;
+    return id;
+}
+
+// Device address of g_compact_scratch in the current context: looked up
+// with the context current on its first use, then taken from the cache.
 cudaError_t scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_cache.mu);
+    unsigned long long id = current_context_id();
+    if (id) {
+        for (int i = 0; i < ScratchCache::kSlots; ++i)
+            if (g_cache.ids[i] == id) {
+                *out = g_cache.addr[i];
+                return cudaSuccess;
+            }
+    }
+    void *p = nullptr;
+    // Makes the runtime's context current when none was (its first call on
+    // this thread), so the id read after it names the context of p.
+    cudaError_t e = cudaGetSymbolAddress(&p, g_compact_scratch);
     if (e != cudaSuccess)
         return e;
-    if (dev < 0 || dev >= kNoallocMaxDevices)
-        return cudaErrorInvalidDevice;
-    void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        e = cudaGetSymbolAddress(&p, g_compact_scratch);
-        if (e != cudaSuccess)
-            return e;
-        g_scratch_addr[dev].store(p, std::memory_order_release);
+    id = current_context_id();
+    if (id) {
+        const int slot = g_cache.next;
+        g_cache.next = (slot + 1) % ScratchCache::kSlots;
+        g_cache.ids[slot] = id;
+        g_cache.addr[slot] = p;
     }
     *out = p;
     return cudaSuccess;

@@ -19,9 +19,12 @@ __host__ __device__ inline size_t groups_of(size_t n) { return (n + 31) / 32; }
 // status code.
 shouji_status cuda_status(cudaError_t e);
 
-// Launchers (argument checks are done by the C-ABI layer).
+// Launchers (argument checks are done by the C-ABI layer).  Without an N
+// mask the pack sets *nflag (device), or the library's flag when nflag is
+// null, when it reads an 'N'.
 cudaError_t launch_pack(const uint8_t *seqs, uint64_t stride, size_t n, int m,
-                        uint32_t *packed, uint32_t *nmask, cudaStream_t s);
+                        uint32_t *packed, uint32_t *nmask, cudaStream_t s,
+                        unsigned int *nflag = nullptr);
 // Synchronizes the device, then reads and resets the count of bounded
 // device waits that ran out (pack staging and the fused pack + filter).
 cudaError_t take_wait_failures(uint32_t *count);
@@ -40,11 +43,24 @@ bool pack_filter_fusable(int m, int E);
 cudaError_t launch_pack_filter(const uint8_t *reads, const uint8_t *refs, size_t n, int m, int E,
                                uint32_t *packed_r, uint32_t *packed_t, uint32_t *accept,
                                uint8_t *count, cudaStream_t s);
+// Whether launch_pack_filter would run the fused kernel for length m and
+// threshold E (pack_filter_fusable and the compiled register count).
+cudaError_t pack_filter_kernel_applies(int m, int E, bool *applies);
+// Read and reset the flags that packs without N masks set when they read an
+// 'N' (no sync): standalone packs, the fused kernel, the batched packs.
+cudaError_t take_pack_unmasked_n(uint32_t *seen);
+cudaError_t take_fused_unmasked_n(uint32_t *seen);
+cudaError_t take_batch_unmasked_n(uint32_t *seen);
+// Synchronizes the device, then reads and resets all three (nonzero: seen).
+cudaError_t take_unmasked_n(uint32_t *seen);
 // Reads and resets the fused kernel's count of waits that ran out (no sync).
 cudaError_t take_fused_wait_failures(uint32_t *count);
 // Runs the pack on 1024 sequences with every staging wait made to run out;
 // writes the failures counted.
 cudaError_t selftest_pack_wait(uint32_t *failures);
+
+// Measured lane-ops per SM clock of one instruction kind (SHOUJI_PROBE_*).
+cudaError_t alu_probe(int op, double *rate);
 
 struct FilterArgs {
     const uint2 *reads, *refs;               // packed pairs (hi, lo) words

@@ -34,12 +34,24 @@ constexpr int kPackSeqs = 256;  // 8 lanes
 
 enum CopyMode { kCopyVec16 = 0, kCopyVec4 = 1, kCopyRows = 2 };
 
+// Set when a pack without an N mask read an 'N' (see shouji_unmasked_n),
+// unless the caller gave a flag word of its own.
+__device__ unsigned int g_pack_unmasked_n;
+
+__device__ __forceinline__ void flag_unmasked_n(unsigned int *nflag)
+{
+    if (nflag)
+        *nflag = 1u;
+    else
+        g_pack_unmasked_n = 1u;
+}
+
 // ALIGNED: m % 4 == 0, so every 4-position word of a row is word-aligned.
 template <bool WITH_N, bool ALIGNED>
 __global__ void __launch_bounds__(kPackThreads)
 pack_kernel(const uint8_t *__restrict__ seqs, uint64_t stride, size_t n, int m,
             uint32_t *__restrict__ packed, uint32_t *__restrict__ nmask, int copy_mode,
-            int rot_step)
+            int rot_step, unsigned int *nflag)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     uint8_t *sb = reinterpret_cast<uint8_t *>(sm);
@@ -99,7 +111,10 @@ pack_kernel(const uint8_t *__restrict__ seqs, uint64_t stride, size_t n, int m,
         sb[b] = 0;
     __syncthreads();
 
-    pack_transpose<WITH_N, ALIGNED>(sm, m, m, tile, lane0, packed, nmask, rot_step, kPackThreads);
+    const uint32_t seen =
+        pack_transpose<WITH_N, ALIGNED>(sm, m, m, tile, lane0, packed, nmask, rot_step, kPackThreads);
+    if (!WITH_N && __syncthreads_or(has_n_bytes(seen)) && tid == 0)
+        flag_unmasked_n(nflag);
 }
 
 // Bounded waits of pack_stream_kernel that ran out (see shouji_wait_failures).
@@ -120,7 +135,7 @@ template <bool WITH_N, bool ALIGNED>
 __global__ void __launch_bounds__(kPackThreads)
 pack_stream_kernel(const uint8_t *__restrict__ seqs, size_t n, int m,
                    uint32_t *__restrict__ packed, uint32_t *__restrict__ nmask, int rot_step,
-                   size_t n_blocks, int buf_bytes, uint32_t extra_tx)
+                   size_t n_blocks, int buf_bytes, uint32_t extra_tx, unsigned int *nflag)
 {
     extern __shared__ __align__(128) uint32_t sm[];
     __shared__ __align__(8) uint64_t full[2];
@@ -174,16 +189,21 @@ pack_stream_kernel(const uint8_t *__restrict__ seqs, size_t n, int m,
             }
             return;
         }
-        pack_transpose<WITH_N, ALIGNED>(reinterpret_cast<const uint32_t *>(buf), m, m,
-                                        seq0 / kTile, (int)((seq0 % kTile) / 32), packed, nmask,
-                                        rot_step, kPackThreads);
-        __syncthreads();  // the buffer may be refilled
+        const uint32_t seen = pack_transpose<WITH_N, ALIGNED>(
+            reinterpret_cast<const uint32_t *>(buf), m, m, seq0 / kTile,
+            (int)((seq0 % kTile) / 32), packed, nmask, rot_step, kPackThreads);
+        // the buffer may be refilled after this barrier
+        if (WITH_N)
+            __syncthreads();
+        else if (__syncthreads_or(has_n_bytes(seen)) && tid == 0)
+            flag_unmasked_n(nflag);
     }
 }
 
 template <bool WITH_N, bool ALIGNED>
 cudaError_t launch_stream_ta(const uint8_t *seqs, size_t n, int m, uint32_t *packed,
-                             uint32_t *nmask, int rot, cudaStream_t s, uint32_t extra_tx = 0)
+                             uint32_t *nmask, int rot, cudaStream_t s, uint32_t extra_tx = 0,
+                             unsigned int *nflag = nullptr)
 {
     // one buffer: 256 rows of m bytes and 16 bytes of zero padding, rounded
     // up to 128 bytes
@@ -205,22 +225,22 @@ cudaError_t launch_stream_ta(const uint8_t *seqs, size_t n, int m, uint32_t *pac
     const size_t full = (size_t)sms * (per_sm > 0 ? per_sm : 1);
     const unsigned grid = (unsigned)(n_blocks < full ? n_blocks : full);
     pack_stream_kernel<WITH_N, ALIGNED><<<grid, kPackThreads, smem, s>>>(
-        seqs, n, m, packed, nmask, rot, n_blocks, buf_bytes, extra_tx);
+        seqs, n, m, packed, nmask, rot, n_blocks, buf_bytes, extra_tx, nflag);
     return cudaGetLastError();
 }
 
 template <bool WITH_N>
 cudaError_t launch_stream_t(const uint8_t *seqs, size_t n, int m, uint32_t *packed,
-                            uint32_t *nmask, int rot, cudaStream_t s)
+                            uint32_t *nmask, int rot, cudaStream_t s, unsigned int *nflag)
 {
     if (m % 4 == 0)
-        return launch_stream_ta<WITH_N, true>(seqs, n, m, packed, nmask, rot, s);
-    return launch_stream_ta<WITH_N, false>(seqs, n, m, packed, nmask, rot, s);
+        return launch_stream_ta<WITH_N, true>(seqs, n, m, packed, nmask, rot, s, 0, nflag);
+    return launch_stream_ta<WITH_N, false>(seqs, n, m, packed, nmask, rot, s, 0, nflag);
 }
 
 template <bool WITH_N>
 cudaError_t launch_pack_t(const uint8_t *seqs, uint64_t stride, size_t n, int m,
-                          uint32_t *packed, uint32_t *nmask, cudaStream_t s)
+                          uint32_t *packed, uint32_t *nmask, cudaStream_t s, unsigned int *nflag)
 {
     const size_t smem = (size_t)kPackSeqs * m + 16;
     const size_t blocks = tiles_of(n) * (kTile / kPackSeqs);
@@ -234,21 +254,21 @@ cudaError_t launch_pack_t(const uint8_t *seqs, uint64_t stride, size_t n, int m,
     const int rot = rotation_step(m);
     cudaError_t e;
     if (mode == kCopyVec16)
-        return launch_stream_t<WITH_N>(seqs, n, m, packed, nmask, rot, s);
+        return launch_stream_t<WITH_N>(seqs, n, m, packed, nmask, rot, s, nflag);
     if (m % 4 == 0) {
         e = cudaFuncSetAttribute(pack_kernel<WITH_N, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
         pack_kernel<WITH_N, true><<<(unsigned)blocks, kPackThreads, smem, s>>>(
-            seqs, stride, n, m, packed, nmask, mode, rot);
+            seqs, stride, n, m, packed, nmask, mode, rot, nflag);
     } else {
         e = cudaFuncSetAttribute(pack_kernel<WITH_N, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
         pack_kernel<WITH_N, false><<<(unsigned)blocks, kPackThreads, smem, s>>>(
-            seqs, stride, n, m, packed, nmask, mode, rot);
+            seqs, stride, n, m, packed, nmask, mode, rot, nflag);
     }
     return cudaGetLastError();
 }
@@ -256,11 +276,23 @@ cudaError_t launch_pack_t(const uint8_t *seqs, uint64_t stride, size_t n, int m,
 }  // namespace
 
 cudaError_t launch_pack(const uint8_t *seqs, uint64_t stride, size_t n, int m,
-                        uint32_t *packed, uint32_t *nmask, cudaStream_t s)
+                        uint32_t *packed, uint32_t *nmask, cudaStream_t s, unsigned int *nflag)
 {
     if (nmask)
-        return launch_pack_t<true>(seqs, stride, n, m, packed, nmask, s);
-    return launch_pack_t<false>(seqs, stride, n, m, packed, nmask, s);
+        return launch_pack_t<true>(seqs, stride, n, m, packed, nmask, s, nullptr);
+    return launch_pack_t<false>(seqs, stride, n, m, packed, nmask, s, nflag);
+}
+
+cudaError_t take_pack_unmasked_n(uint32_t *seen)
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_pack_unmasked_n, sizeof v);
+    if (e == cudaSuccess && v) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_pack_unmasked_n, &zero, sizeof zero);
+    }
+    *seen = v;
+    return e;
 }
 
 cudaError_t take_wait_failures(uint32_t *count)

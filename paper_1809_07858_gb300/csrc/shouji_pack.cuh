@@ -28,23 +28,37 @@ __device__ __forceinline__ uint32_t n_bytes(uint32_t w)
     return ~t & 0x80808080u;
 }
 
+// Packing without an N mask reads an 'N' as 'G' (both have bits 2 and 1
+// set).  The packs therefore OR together every staged word they read and
+// look at bit 3 of each byte: it is clear in 'A', 'C', 'G' and 'T' and set
+// in 'N' (0x4E) and 'n'.  A block in which it is set is counted for
+// shouji_unmasked_n(), so that a caller learns that such results differ from
+// the ones an N mask gives.
+__device__ __forceinline__ bool has_n_bytes(uint32_t seen) { return (seen & 0x08080808u) != 0; }
+
 // Phase 2 of the pack: the staged rows (row r = sequence r of the block, at
 // byte r * rs of sm, m bases each) -> the bit-sliced words of lanes
 // lane0 .. lane0+LANES-1 of a tile.  A thread owns (lane, 4 consecutive
 // positions); a warp covers LANES lanes x 32/LANES position quads.
 // ALIGNED: rs % 4 == 0, so every 4-position word of a row is word-aligned.
 // The items are shared out among nthreads threads, this one being number tid.
+// Without WITH_N, returns the OR of the bases this thread read (bytes past
+// the end of a row left out), for has_n_bytes; with it, 0.
 template <bool WITH_N, bool ALIGNED, int LANES = 8>
-__device__ __forceinline__ void pack_transpose_by(const uint32_t *__restrict__ sm, int m, int rs,
-                                                  size_t tile, int lane0,
-                                                  uint32_t *__restrict__ packed,
-                                                  uint32_t *__restrict__ nmask, int rot_step,
-                                                  int nthreads, int tid)
+__device__ __forceinline__ uint32_t pack_transpose_by(const uint32_t *__restrict__ sm, int m,
+                                                      int rs, size_t tile, int lane0,
+                                                      uint32_t *__restrict__ packed,
+                                                      uint32_t *__restrict__ nmask, int rot_step,
+                                                      int nthreads, int tid)
 {
     const int J = (m + 3) >> 2;
+    uint32_t seen = 0;
     for (int item = tid; item < LANES * J; item += nthreads) {
         const int l = item % LANES, j = item / LANES;
         const int rot = (rot_step * l) & 31;     // visit sequence (s + rot) % 32 at step s
+        // bytes of the item's words that hold bases (the last word of a row
+        // may run past its end)
+        const uint32_t keep = 4 * j + 4 <= m ? ~0u : (1u << (8 * (m - 4 * j))) - 1u;
         uint32_t yh[4], yl[4], yn[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -63,6 +77,8 @@ __device__ __forceinline__ void pack_transpose_by(const uint32_t *__restrict__ s
                 lo |= ((w >> 1) & 0x01010101u) << u;
                 if (WITH_N)
                     nn |= (n_bytes(w) >> 7) << u;
+                else
+                    seen |= w & keep;
             }
             yh[t] = h;
             yl[t] = lo;
@@ -87,6 +103,7 @@ __device__ __forceinline__ void pack_transpose_by(const uint32_t *__restrict__ s
             }
         }
     }
+    return seen;
 }
 
 // pack_transpose_by for 8 lanes of rows with an odd number W = m / 4 of
@@ -97,14 +114,16 @@ __device__ __forceinline__ void pack_transpose_by(const uint32_t *__restrict__ s
 // when W is odd), the row address is found once per 4 words, and each
 // base's bits are shifted straight to their place (a left shift where
 // possible) and merged with one mask-and-or per plane.  The output words are
-// rotated back by 4l, as in pack_transpose_by.
-__device__ __forceinline__ void pack_transpose_w_odd(const uint32_t *__restrict__ sm, int m,
-                                                     size_t tile, int lane0,
-                                                     uint32_t *__restrict__ packed,
-                                                     int nthreads, int tid)
+// rotated back by 4l, as in pack_transpose_by.  Returns the OR of the words
+// read, for has_n_bytes.
+__device__ __forceinline__ uint32_t pack_transpose_w_odd(const uint32_t *__restrict__ sm, int m,
+                                                         size_t tile, int lane0,
+                                                         uint32_t *__restrict__ packed,
+                                                         int nthreads, int tid)
 {
     constexpr int LANES = 8;
     const int W = m >> 2;
+    uint32_t seen = 0;
     for (int item = tid; item < LANES * W; item += nthreads) {
         const int l = item % LANES, j = item / LANES;
         const uint32_t *lane_rows = sm + 32 * l * W + j;  // word j of the lane's first row
@@ -119,6 +138,7 @@ __device__ __forceinline__ void pack_transpose_w_odd(const uint32_t *__restrict_
                 for (int v = 0; v < 4; ++v) {
                     const int u = 4 * half + v;  // bit of each byte that step 8t + u fills
                     const uint32_t w = grp[v * W];
+                    seen |= w;
                     // bit 2 (hi) and bit 1 (lo) of each byte, moved to bit u
                     const uint32_t xh = u >= 2 ? w << (u - 2) : w >> (2 - u);
                     const uint32_t xl = u >= 1 ? w << (u - 1) : w >> 1;
@@ -141,18 +161,19 @@ __device__ __forceinline__ void pack_transpose_w_odd(const uint32_t *__restrict_
                 make_uint2(__funnelshift_l(H[q], H[q], rot), __funnelshift_l(L[q], L[q], rot));
         }
     }
+    return seen;
 }
 
 // pack_transpose_by with the threads of the CTA in threadIdx.x order.
 template <bool WITH_N, bool ALIGNED, int LANES = 8>
-__device__ __forceinline__ void pack_transpose(const uint32_t *__restrict__ sm, int m, int rs,
-                                               size_t tile, int lane0,
-                                               uint32_t *__restrict__ packed,
-                                               uint32_t *__restrict__ nmask, int rot_step,
-                                               int nthreads)
+__device__ __forceinline__ uint32_t pack_transpose(const uint32_t *__restrict__ sm, int m, int rs,
+                                                   size_t tile, int lane0,
+                                                   uint32_t *__restrict__ packed,
+                                                   uint32_t *__restrict__ nmask, int rot_step,
+                                                   int nthreads)
 {
-    pack_transpose_by<WITH_N, ALIGNED, LANES>(sm, m, rs, tile, lane0, packed, nmask, rot_step,
-                                              nthreads, (int)threadIdx.x);
+    return pack_transpose_by<WITH_N, ALIGNED, LANES>(sm, m, rs, tile, lane0, packed, nmask,
+                                                     rot_step, nthreads, (int)threadIdx.x);
 }
 
 // Per-lane rotation step c with c * (rs/4) = 32/lanes (mod 32) when such a c
@@ -263,15 +284,20 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
     asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
     return t;
 }
+// Tests a bounded wait makes at most: one test sleeps at most kSuspendNs,
+// so the wait ends within about 2 s even should the timer stand still.
+constexpr int kMaxWaitTests = 20000;
+static_assert((uint64_t)kMaxWaitTests * kSuspendNs <= 2100000000ull,
+              "a bounded wait must end within about 2 s");
 // Waits for the phase of `bar` with the given parity to complete; gives up
-// (false) after about a second, or after 2^26 tests should the timer stand
-// still (a test sleeps at most kSuspendNs, so that is the later bound).
+// (false) after about a second by the global timer, or after kMaxWaitTests
+// tests, whichever comes first.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
     if (mbar_try_wait(bar, parity))
         return true;
     const uint64_t t0 = globaltimer_ns();
-    for (int it = 0; it < (1 << 26); ++it) {
+    for (int it = 0; it < kMaxWaitTests; ++it) {
         if (mbar_try_wait(bar, parity))
             return true;
         if (globaltimer_ns() - t0 > 1000000000ull)

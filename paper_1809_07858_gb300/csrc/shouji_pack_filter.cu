@@ -15,18 +15,25 @@
 //    two groups' transpositions overlap.  A block costs a group about the
 //    latency of one transposition item plus two barriers, whatever its size,
 //    so two groups double the pack rate.
-//  - 8 consumer warps filter the tiles already packed, each taking every 8th
-//    tile of the range.
-// A tile is handed over through two mbarriers per consumer: `ready` (all 512
+//  - 8 consumer warps filter the tiles already packed; a consumer that is
+//    done with a tile takes the next one from a counter in shared memory, so
+//    the tiles go to whichever consumer is free.
+// Tiles go through a queue of kSlots slots: tile r of the CTA's range uses
+// slot r % kSlots, whose two mbarriers hand it over: `ready` (all 512
 // producer threads arrive once their words of the tile are written) and
-// `freed` (the consumer's 32 threads arrive once they have filtered it).  The
-// producers complete a consumer's tile k only after its tile k-1 is freed, so
-// they run at most one tile ahead of each consumer (the packed words in
-// flight stay within L2) and the parity of each barrier phase is never
-// ambiguous.  The producers wait only on consumer steps that depend on
-// phases the producers completed before, so the hand-over cannot deadlock;
-// every wait is bounded all the same (about a second), and a wait that runs
-// out ends the warps concerned and is counted for shouji_wait_failures().
+// `freed` (the consumer's 32 threads arrive once they have filtered it).
+// The producers complete tile r only after tile r - kSlots is freed, so at
+// most kSlots packed tiles are in flight per CTA (they stay within L2) and a
+// slot's phases never run two ahead of a waiter.  With kSlots at least the
+// number of consumers, the tile r - kSlots has always been packed when a
+// consumer takes tile r (consumers take tiles in order and each holds one),
+// so the parity of each phase a consumer waits for is never ambiguous.  A
+// slow consumer holds up only its own slot: the producers go on packing the
+// next tiles for the others.  The producers wait only on consumer steps that
+// depend on phases the producers completed before, so the hand-over cannot
+// deadlock; every wait is bounded all the same (about a second), and a wait
+// that runs out ends the warps concerned and is counted for
+// shouji_wait_failures().
 //
 // Registers: the CTA is launched with 768 threads at 80 registers (61,440 of
 // the SM's 65,536).  The producers give theirs down to 56 and the consumers
@@ -46,6 +53,11 @@ namespace {
 using namespace packdev;
 
 constexpr int kConsumers = 8;                      // filter warps per CTA
+#ifndef SHOUJI_FUSED_SLOTS
+#define SHOUJI_FUSED_SLOTS 10
+#endif
+constexpr int kSlots = SHOUJI_FUSED_SLOTS;         // tiles in flight per CTA
+static_assert(kSlots >= kConsumers, "a consumer's wait needs the slot's previous phase done");
 constexpr int kGroups = 2;                         // producer groups
 constexpr int kGroupThreads = 256;                 // 8 warps per group
 constexpr int kProducers = kGroups * kGroupThreads;
@@ -66,6 +78,9 @@ constexpr int kRingBytes = 200 * 1024;             // shared memory for both rin
 static_assert(SHOUJI_FUSED_MAX_E == 5, "consumers have 128 registers");
 
 __device__ unsigned int g_fused_wait_failures;
+// Set when the producers read an 'N' (the fused kernel has no N masks; see
+// shouji_unmasked_n).
+__device__ unsigned int g_fused_unmasked_n;
 
 // Named barrier of producer group g (barrier 0 is __syncthreads).
 __device__ __forceinline__ void group_sync(int g)
@@ -141,6 +156,7 @@ __device__ void produce(const FusedArgs &a, uint8_t *ring, uint64_t *full, uint6
             issue(issued);
     size_t j = 0;        // on failure: the first job whose copy may be in flight
     bool failed = false;
+    uint32_t seen = 0;   // OR of the bases this thread read
     for (; j < njobs; ++j) {
         if (issued < njobs) {
             if (gtid == 0) {
@@ -166,45 +182,58 @@ __device__ void produce(const FusedArgs &a, uint8_t *ring, uint64_t *full, uint6
         uint32_t *dst = (i / kHalfBlocks) % 2 ? a.packed_t : a.packed_r;
         const int lane0 = (int)(i % kHalfBlocks) * kBlockLanes;
         if constexpr (LAYOUT == 2)
-            pack_transpose_w_odd(reinterpret_cast<const uint32_t *>(buf), a.m, t, lane0, dst,
-                                 kGroupThreads, gtid);
+            seen |= pack_transpose_w_odd(reinterpret_cast<const uint32_t *>(buf), a.m, t, lane0,
+                                         dst, kGroupThreads, gtid);
         else
-            pack_transpose_by<false, LAYOUT == 1, kBlockLanes>(
+            seen |= pack_transpose_by<false, LAYOUT == 1, kBlockLanes>(
                 reinterpret_cast<const uint32_t *>(buf), a.m, a.m, t, lane0, dst, nullptr,
                 a.rot_step, kGroupThreads, gtid);
         if (i % kBlocksPerTile >= kBlocksPerTile - kGroups) {  // the group's last block of t
-            const int w = (int)((t - T0) % kConsumers);
-            const size_t k = (t - T0) / kConsumers;
-            const bool seen = k == 0 || mbar_wait_bounded(&freed[w], (uint32_t)((k - 1) & 1));
-            if (group_sync_or(g, !seen)) {
+            const int slot = (int)((t - T0) % kSlots);
+            const size_t k = (t - T0) / kSlots;
+            const bool was_freed =
+                k == 0 || mbar_wait_bounded(&freed[slot], (uint32_t)((k - 1) & 1));
+            if (group_sync_or(g, !was_freed)) {
                 failed = true;
                 ++j;
                 break;
             }
-            mbar_arrive(&ready[w]);  // release: this thread's words of tile t
+            mbar_arrive(&ready[slot]);  // release: this thread's words of tile t
         }
         group_sync(g);  // buffer b may be refilled
     }
-    if (failed && gtid == 0) {
-        atomicAdd(&g_fused_wait_failures, 1u);
-        for (size_t q = j; q < issued; ++q)  // copies that may still be in flight
-            mbar_wait_bounded(&myfull[q % a.ring], (uint32_t)((q / a.ring) & 1));
+    if (failed) {
+        if (gtid == 0) {
+            atomicAdd(&g_fused_wait_failures, 1u);
+            for (size_t q = j; q < issued; ++q)  // copies that may still be in flight
+                mbar_wait_bounded(&myfull[q % a.ring], (uint32_t)((q / a.ring) & 1));
+        }
+        return;
     }
+    // every thread of the group gets here (a failure is seen by the whole group)
+    if (group_sync_or(g, has_n_bytes(seen)) && gtid == 0)
+        g_fused_unmasked_n = 1u;
 }
 
 template <int E>
-__device__ void consume(const FusedArgs &a, uint64_t *ready, uint64_t *freed, size_t T0,
-                        size_t T1)
+__device__ void consume(const FusedArgs &a, uint64_t *ready, uint64_t *freed,
+                        unsigned int *next_tile, size_t T0, size_t T1)
 {
     constexpr int U = SHOUJI_FILTER_U;
-    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int lane = (int)threadIdx.x & 31;
     const size_t n_groups = groups_of(a.n);
     const int m = a.m;
-    for (size_t k = 0;; ++k) {
-        const size_t t = T0 + w + k * kConsumers;
+    for (;;) {
+        unsigned int r = 0;  // the next tile of the range, the same in the whole warp
+        if (lane == 0)
+            r = atomicAdd(next_tile, 1u);
+        r = __shfl_sync(~0u, r, 0);
+        const size_t t = T0 + r;
         if (t >= T1)
             break;
-        const bool ok = mbar_wait_bounded(&ready[w], (uint32_t)(k & 1));
+        const int slot = (int)(r % kSlots);
+        const uint32_t k = r / kSlots;
+        const bool ok = mbar_wait_bounded(&ready[slot], k & 1u);
         if (!__all_sync(~0u, ok)) {
             if (lane == 0)
                 atomicAdd(&g_fused_wait_failures, 1u);
@@ -212,7 +241,7 @@ __device__ void consume(const FusedArgs &a, uint64_t *ready, uint64_t *freed, si
         }
         const size_t grp = t * kLanes + lane;  // this thread's group of 32 pairs
         if (grp >= n_groups) {
-            mbar_arrive(&freed[w]);
+            mbar_arrive(&freed[slot]);
             continue;
         }
         const size_t base = t * (size_t)m * kLanes + lane;
@@ -246,7 +275,7 @@ __device__ void consume(const FusedArgs &a, uint64_t *ready, uint64_t *freed, si
                     a.count[first + b] = (uint8_t)(cw[b >> 2] >> (8 * (b & 3)));
             }
         }
-        mbar_arrive(&freed[w]);  // done with tile t
+        mbar_arrive(&freed[slot]);  // done with tile t
     }
 }
 
@@ -254,15 +283,16 @@ template <int E, int LAYOUT>
 __global__ void __launch_bounds__(kFusedThreads, 1) pack_filter_kernel(FusedArgs a)
 {
     extern __shared__ __align__(128) uint8_t ring[];
-    __shared__ __align__(8) uint64_t full[kGroups * kMaxRing], ready[kConsumers],
-        freed[kConsumers];
+    __shared__ __align__(8) uint64_t full[kGroups * kMaxRing], ready[kSlots], freed[kSlots];
+    __shared__ unsigned int next_tile;
     if (threadIdx.x == 0) {
         for (int b = 0; b < kGroups * kMaxRing; ++b)
             mbar_init(&full[b], 1);
-        for (int w = 0; w < kConsumers; ++w) {
-            mbar_init(&ready[w], kProducers);
-            mbar_init(&freed[w], 32);
+        for (int q = 0; q < kSlots; ++q) {
+            mbar_init(&ready[q], kProducers);
+            mbar_init(&freed[q], 32);
         }
+        next_tile = 0;
         mbar_init_fence();
     }
     __syncthreads();
@@ -275,17 +305,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) pack_filter_kernel(FusedArgs
     // warpgroups 0-1 consume, 2-5 produce
     if (threadIdx.x < kConsumers * 32) {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kConsumerRegs));
-        consume<E>(a, ready, freed, T0, T1);
+        consume<E>(a, ready, freed, &next_tile, T0, T1);
     } else {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kProducerRegs));
         produce<LAYOUT>(a, ring, full, ready, freed, T0, T1);
     }
 }
 
+// The register split above holds only at exactly kLaunchRegs per thread:
+// cudaErrorNotSupported when the compiled kernel has another count.
 template <int E, int LAYOUT>
-cudaError_t launch_fused_ta(const FusedArgs &a, cudaStream_t s)
+cudaError_t check_regs()
 {
-    // The register split above holds only at exactly kLaunchRegs per thread.
     static int regs = -1;
     if (regs < 0) {
         cudaFuncAttributes fa;
@@ -294,8 +325,27 @@ cudaError_t launch_fused_ta(const FusedArgs &a, cudaStream_t s)
             return e;
         regs = fa.numRegs;
     }
-    if (regs != kLaunchRegs)
-        return cudaErrorNotSupported;
+    return regs == kLaunchRegs ? cudaSuccess : cudaErrorNotSupported;
+}
+
+int layout_of(int m) { return m % 8 == 4 ? 2 : m % 4 == 0 ? 1 : 0; }
+
+template <int E>
+cudaError_t check_regs_E(int m)
+{
+    switch (layout_of(m)) {
+    case 2: return check_regs<E, 2>();
+    case 1: return check_regs<E, 1>();
+    default: return check_regs<E, 0>();
+    }
+}
+
+template <int E, int LAYOUT>
+cudaError_t launch_fused_ta(const FusedArgs &a, cudaStream_t s)
+{
+    cudaError_t e0 = check_regs<E, LAYOUT>();
+    if (e0 != cudaSuccess)
+        return e0;
     const size_t smem = (size_t)kGroups * a.ring * a.buf_bytes;
     cudaError_t e = cudaFuncSetAttribute(pack_filter_kernel<E, LAYOUT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -322,6 +372,12 @@ cudaError_t launch_fused_E(const FusedArgs &a, cudaStream_t s)
     return launch_fused_ta<E, 0>(a, s);
 }
 
+using CheckFn = cudaError_t (*)(int);
+constexpr CheckFn kCheck[SHOUJI_FUSED_MAX_E + 1] = {
+    &check_regs_E<0>, &check_regs_E<1>, &check_regs_E<2>,
+    &check_regs_E<3>, &check_regs_E<4>, &check_regs_E<5>,
+};
+
 using FusedFn = cudaError_t (*)(const FusedArgs &, cudaStream_t);
 constexpr FusedFn kFused[SHOUJI_FUSED_MAX_E + 1] = {
     &launch_fused_E<0>, &launch_fused_E<1>, &launch_fused_E<2>,
@@ -344,6 +400,18 @@ bool pack_filter_fusable(int m, int E)
     return E >= 0 && E <= SHOUJI_FUSED_MAX_E && m >= 1 && ring_for(m, buf_bytes) >= 2;
 }
 
+cudaError_t pack_filter_kernel_applies(int m, int E, bool *applies)
+{
+    *applies = false;
+    if (!pack_filter_fusable(m, E))
+        return cudaSuccess;
+    const cudaError_t e = kCheck[E](m);
+    if (e == cudaErrorNotSupported)
+        return cudaSuccess;
+    *applies = e == cudaSuccess;
+    return e;
+}
+
 cudaError_t launch_pack_filter(const uint8_t *reads, const uint8_t *refs, size_t n, int m, int E,
                                uint32_t *packed_r, uint32_t *packed_t, uint32_t *accept,
                                uint8_t *count, cudaStream_t s)
@@ -362,6 +430,18 @@ cudaError_t launch_pack_filter(const uint8_t *reads, const uint8_t *refs, size_t
     a.rot_step = rotation_step(m, kBlockLanes);
     a.ring = ring_for(m, a.buf_bytes);
     return kFused[E](a, s);
+}
+
+cudaError_t take_fused_unmasked_n(uint32_t *seen)
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_fused_unmasked_n, sizeof v);
+    if (e == cudaSuccess && v) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_fused_unmasked_n, &zero, sizeof zero);
+    }
+    *seen = v;
+    return e;
 }
 
 cudaError_t take_fused_wait_failures(uint32_t *count)

@@ -32,6 +32,8 @@ struct shouji_pipeline {
     void *d_ws[2];
     uint32_t *d_idx;
     uint32_t *d_total;
+    unsigned int *d_nflag;  // per stream: a pack without N masks read an 'N'
+
     uint32_t *h_total;  // pinned
 };
 
@@ -73,6 +75,7 @@ void release(shouji_pipeline *p)
     }
     cudaFree(p->d_idx);
     cudaFree(p->d_total);
+    cudaFree(p->d_nflag);
     if (p->h_total)
         cudaFreeHost(p->h_total);
     if (p->ev_compact)
@@ -128,6 +131,7 @@ shouji_status shouji_pipeline_create(uint32_t m, size_t chunk_pairs, size_t max_
     if (ok && max_pairs)
         ok = cudaMalloc(&p->d_idx, max_pairs * sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&p->d_total, sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->d_nflag, 2 * sizeof(unsigned int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&p->h_total, sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&p->ev_compact, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -170,6 +174,8 @@ shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, cons
         SHOUJI_TRY(cudaMemsetAsync(p->d_total, 0, sizeof(uint32_t), p->st[0]));
         SHOUJI_TRY(cudaEventRecord(p->ev_compact, p->st[0]));
     }
+    for (int k = 0; k < 2; ++k)
+        SHOUJI_TRY(cudaMemsetAsync(p->d_nflag + k, 0, sizeof(unsigned int), p->st[k]));
     int slot = 0;
     for (size_t base = 0; base < n_pairs; base += p->chunk, slot ^= 1) {
         cudaStream_t s = p->st[slot];
@@ -186,9 +192,9 @@ shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, cons
                                          nc, cudaMemcpyHostToDevice, s));
         }
         SHOUJI_TRY(launch_pack(p->d_reads[slot], m, nc, (int)m, p->d_pr[slot],
-                               p->with_n ? p->d_nr[slot] : nullptr, s));
+                               p->with_n ? p->d_nr[slot] : nullptr, s, p->d_nflag + slot));
         SHOUJI_TRY(launch_pack(p->d_refs[slot], m, nc, (int)m, p->d_pt[slot],
-                               p->with_n ? p->d_nt[slot] : nullptr, s));
+                               p->with_n ? p->d_nt[slot] : nullptr, s, p->d_nflag + slot));
         FilterArgs a;
         a.reads = reinterpret_cast<const uint2 *>(p->d_pr[slot]);
         a.refs = reinterpret_cast<const uint2 *>(p->d_pt[slot]);
@@ -229,10 +235,15 @@ shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, cons
         for (size_t w = 0; w < words; ++w)
             total += (uint64_t)__builtin_popcount(accept[w]);
     }
+    unsigned int nflag[2] = {0, 0};
+    if (!p->with_n)
+        SHOUJI_TRY(cudaMemcpy(nflag, p->d_nflag, sizeof nflag, cudaMemcpyDeviceToHost));
+    const bool unmasked_n = nflag[0] || nflag[1];
 #undef SHOUJI_TRY
     if (n_accepted)
         *n_accepted = total;
-    return SHOUJI_OK;
+    // Results are complete either way; without N masks an 'N' was read as 'G'.
+    return unmasked_n ? SHOUJI_EINVAL : SHOUJI_OK;
 }
 
 }  // extern "C"

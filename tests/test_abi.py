@@ -100,3 +100,25 @@ def test_host_argument_checks_return_einval():
     assert lib.shouji_compact(fake, 1000, fake, fake, ctypes.c_void_p(0x1008), 1 << 20, None) == EINVAL
     assert lib.shouji_compact(fake, 1 << 32, fake, fake, fake, 1 << 30, None) == EINVAL
     assert lib.shouji_compact(None, 1000, fake, fake, fake, 1 << 20, None) == EINVAL
+
+
+def test_query_and_probe_argument_checks():
+    lib = sj.load_library()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced
+    EINVAL = 1
+    f = ctypes.c_int(7)
+    u64 = ctypes.c_uint64
+    pff = lib.shouji_pack_filter_fused
+    assert pff(fake, fake, u64(100), 100, 5, None) == EINVAL
+    assert pff(fake, fake, u64(100), 0, 5, ctypes.byref(f)) == EINVAL and f.value == 0
+    assert pff(fake, fake, u64(99), 100, 5, ctypes.byref(f)) == EINVAL
+    assert pff(fake, fake, u64(100), 100, 32, ctypes.byref(f)) == EINVAL
+    # rows that are not contiguous or not on 16 bytes never take the fused kernel;
+    # this needs no device
+    f.value = 7
+    assert pff(fake, fake, u64(112), 100, 5, ctypes.byref(f)) == 0 and f.value == 0
+    f.value = 7
+    assert pff(ctypes.c_void_p(0x1004), fake, u64(100), 100, 5, ctypes.byref(f)) == 0
+    assert f.value == 0
+    assert lib.shouji_unmasked_n(None) == EINVAL
+    assert lib.shouji_batch_timing(None, None, 0) == EINVAL

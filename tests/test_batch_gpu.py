@@ -1,5 +1,7 @@
 """The batched path (mixed lengths and thresholds in one CUDA-graph launch)
 against the oracle, pair by pair: accept bits and counts bit-exact."""
+import os
+
 import numpy as np
 import pytest
 
@@ -17,7 +19,7 @@ def dev():
     return torch.device("cuda:0")
 
 
-def oracle_mixed(reads, refs, lens, Es):
+def oracle_mixed(reads, refs, lens, Es, threads=8):
     """Per pair: the oracle on the first lens[i] bases at threshold Es[i]."""
     n = len(lens)
     acc = np.zeros(n, bool)
@@ -25,7 +27,7 @@ def oracle_mixed(reads, refs, lens, Es):
     for L in np.unique(lens):
         idx = np.flatnonzero(lens == L)
         a, c = oracle.shouji_batch(reads[idx, :L], refs[idx, :L], 0,
-                                   E_per_pair=Es[idx].astype(np.uint8), threads=8)
+                                   E_per_pair=Es[idx].astype(np.uint8), threads=threads)
         acc[idx], cnt[idx] = a, c
     return acc, cnt
 
@@ -128,6 +130,43 @@ def test_tuned_shapes_give_identical_results(tmp_path):
     b2.close()
 
 
+def test_runs_queued_back_to_back_use_their_own_arguments():
+    """Runs alternate between two argument blocks: three batches queued on one
+    stream without waiting (outputs into separate buffers) each give the
+    results they give alone."""
+    d = dev()
+    batches = [mixed_batch(30_000, seed=s) for s in (31, 32, 33)]
+    b = sj.Batch(30_000, 250, 2, 12)
+    outs = []
+    for reads, refs, lens, Es in batches:
+        outs.append(b.run(torch.from_numpy(reads).to(d), torch.from_numpy(refs).to(d),
+                          torch.from_numpy(lens.astype(np.int16)).to(d),
+                          torch.from_numpy(Es).to(d)))
+    torch.cuda.synchronize()
+    for (reads, refs, lens, Es), (acc, cnt) in zip(batches, outs):
+        acc_o, cnt_o = oracle_mixed(reads, refs, lens, Es)
+        assert (accept_bits(acc.cpu().numpy(), len(lens)) == acc_o).all()
+        assert (cnt[:len(lens)].cpu().numpy() == cnt_o).all()
+    b.close()
+
+
+def test_stage_timing_recorded_by_the_graph():
+    reads, refs, lens, Es = mixed_batch(200_000, seed=34)
+    b = sj.Batch(200_000, 250, 2, 12)
+    t0 = b.timing()
+    assert t0["graph"] == -1 and t0["filter_E"] == {}   # before the first run
+    run_batch(b, reads, refs, lens, Es)
+    t = b.timing()
+    assert t["graph"] > 0 and t["filters"] > 0 and t["pack"] > 0
+    assert t["bucketing"] >= 0 and t["finalize"] >= 0
+    parts = t["bucketing"] + t["pack"] + t["filters"] + t["finalize"]
+    assert abs(parts - t["graph"]) <= 0.05 * t["graph"] + 0.02
+    assert sorted(t["filter_E"]) == list(range(2, 13))
+    for E, ms in t["filter_E"].items():
+        assert 0 < ms <= t["filters"] + 1e-3, (E, ms)
+    b.close()
+
+
 def test_unaligned_stride_byte_path():
     reads, refs, lens, Es = mixed_batch(5000, seed=6, stride=251)
     b = sj.Batch(5000, 250, 2, 12)
@@ -138,11 +177,11 @@ def test_unaligned_stride_byte_path():
 
 
 @pytest.mark.slow
-def test_full_size_batch_sampled(host_buffers):
+def test_full_size_batch_every_pair(host_buffers):
     """The benchmark's batched workload at its full size (50M pairs, lengths
     40% 100 / 40% 150 / 20% 250, E uniform in 2..12, unsorted, stride 256) in one
-    graph launch: properties over every pair, and a seeded sample of 300k pairs
-    against the oracle."""
+    graph launch: properties over every pair, and every pair against the
+    oracle (run on all host cores, in chunks)."""
     d = dev()
     n = 50_000_000
     lens, Es = synth.mixed_shape(n, seed=4242)
@@ -159,9 +198,12 @@ def test_full_size_batch_sampled(host_buffers):
     assert invalid == 0
     assert (cnt <= lens).all()
     assert (bits == (cnt <= Es)).all()
-    pick = np.sort(np.random.default_rng(50).choice(n, size=300_000, replace=False))
-    acc_o, cnt_o = oracle_mixed(reads[pick], refs[pick], lens[pick], Es[pick])
-    assert (cnt[pick] == cnt_o).all()
-    assert (bits[pick] == acc_o).all()
     del acc
     torch.cuda.empty_cache()
+    threads = max(1, os.cpu_count() or 1)
+    chunk = 4_000_000
+    for s0 in range(0, n, chunk):
+        sl = slice(s0, min(n, s0 + chunk))
+        acc_o, cnt_o = oracle_mixed(reads[sl], refs[sl], lens[sl], Es[sl], threads=threads)
+        bad = np.flatnonzero((cnt[sl] != cnt_o) | (bits[sl] != acc_o))
+        assert bad.size == 0, "pairs %d.. : %d differ, first %s" % (s0, bad.size, bad[:10] + s0)

@@ -2,24 +2,31 @@
 kernel (csrc/shouji_pack_filter.cu).
 
 Actors: 2 producer groups and 8 filter warps of one CTA, over its range of
-tiles.  Group g packs blocks i = g, g + 2, ... (8 blocks per tile) and, after
-its last block of tile t, waits for `freed[w]` phase k - 1 (k > 0) and then
-arrives on `ready[w]`, where w = t % 8 and k = t // 8.  Filter warp w takes
-tiles w, w + 8, ...: it waits for `ready[w]` phase k, filters the tile and
-arrives on `freed[w]`.  A barrier only knows its current phase; a wait on
-parity P returns as soon as the current phase's parity differs from P, which
-is what the hardware's parity wait does.
+tiles, and a queue of S slots (S is read from the kernel source).  Group g
+packs blocks i = g, g + 2, ... (8 blocks per tile) and, after its last block
+of tile t, waits for `freed[s]` phase k - 1 (k > 0) and then arrives on
+`ready[s]`, where s = t % S and k = t // S.  A filter warp that is free takes
+the next tile r from a shared counter, waits for `ready[r % S]` phase r // S,
+filters the tile and arrives on `freed[r % S]`.  A barrier only knows its
+current phase; a wait on parity P returns as soon as the current phase's
+parity differs from P, which is what the hardware's parity wait does.
 
 Random interleavings check that every tile a filter warp accepts is the one
-it expects, with all its producer arrivals and no arrival of another tile in
-the same phase, and that the actors never deadlock.  The same model without
-the producers' `freed` wait (the planted mistake) must fail the check.
+it took, with all its producer arrivals and no arrival of another tile in the
+same phase, and that the actors never deadlock.  Two planted mistakes must
+fail the check: producers that skip the `freed` wait, and a queue with fewer
+slots than filter warps.
 """
+import os
 import random
+import re
 
 import pytest
 
 GROUPS, CONSUMERS, BLOCKS = 2, 8, 8
+_SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    "paper_1809_07858_gb300", "csrc", "shouji_pack_filter.cu")
+SLOTS = int(re.search(r"#define SHOUJI_FUSED_SLOTS (\d+)", open(_SRC).read()).group(1))
 
 
 class Barrier:
@@ -43,8 +50,9 @@ class Barrier:
 
 
 class Producer:
-    def __init__(self, g, n_tiles, ready, freed, wait_freed=True):
+    def __init__(self, g, n_tiles, ready, freed, slots, wait_freed=True):
         self.g, self.ready, self.freed, self.wait_freed = g, ready, freed, wait_freed
+        self.slots = slots
         self.blocks = list(range(g, n_tiles * BLOCKS, GROUPS))
         self.pos = 0
 
@@ -57,79 +65,118 @@ class Producer:
         i = self.blocks[self.pos]
         if i % BLOCKS >= BLOCKS - GROUPS:
             t = i // BLOCKS
-            w, k = t % CONSUMERS, t // CONSUMERS
-            if self.wait_freed and k > 0 and not self.freed[w].try_wait((k - 1) & 1):
+            s, k = t % self.slots, t // self.slots
+            if self.wait_freed and k > 0 and not self.freed[s].try_wait((k - 1) & 1):
                 return False
-            self.ready[w].arrive(t)
+            self.ready[s].arrive(t)
         self.pos += 1
         return True
 
 
+class Queue:
+    def __init__(self, n_tiles):
+        self.next, self.n_tiles = 0, n_tiles
+
+
 class Consumer:
-    def __init__(self, w, n_tiles, ready, freed, rng):
-        self.w, self.ready, self.freed, self.rng = w, ready, freed, rng
-        self.tiles = list(range(w, n_tiles, CONSUMERS))
-        self.pos = 0
-        self.work = 0  # filter steps left on the current tile
+    def __init__(self, w, queue, ready, freed, slots, rng):
+        self.w, self.q, self.ready, self.freed, self.rng = w, queue, ready, freed, rng
+        self.slots = slots
+        self.tile = None   # the tile taken, not yet accepted
+        self.work = 0      # filter steps left on the accepted tile
+        self.finished = False
+        self.taken = []
 
     def done(self):
-        return self.pos == len(self.tiles)
+        return self.finished
 
     def step(self):
-        k, t = self.pos, self.tiles[self.pos]
-        if self.work == 0:
-            if not self.ready[self.w].try_wait(k & 1):
+        if self.tile is None and self.work == 0:
+            r = self.q.next
+            self.q.next += 1
+            if r >= self.q.n_tiles:
+                self.finished = True
+                return True
+            self.tile = r
+            self.taken.append(r)
+            return True
+        if self.tile is not None:
+            r = self.tile
+            s, k = r % self.slots, r // self.slots
+            if not self.ready[s].try_wait(k & 1):
                 return False
-            r = self.ready[self.w]
-            assert r.phase == k + 1, "warp %d saw phase %d for its tile %d" % (self.w, r.phase, k)
-            assert r.history[k] == {t}, "phase %d of ready[%d] held tiles %s, not %d" % (
-                k, self.w, sorted(r.history[k]), t)
+            b = self.ready[s]
+            assert b.phase == k + 1, "warp %d saw phase %d of slot %d for tile %d" % (
+                self.w, b.phase, s, r)
+            assert b.history[k] == {r}, "phase %d of ready[%d] held tiles %s, not %d" % (
+                k, s, sorted(b.history[k]), r)
             self.work = 1 + self.rng.randrange(12)
+            self.tile = None
+            self.accepted = r
             return True
         self.work -= 1
         if self.work == 0:
-            self.freed[self.w].arrive(t)
-            self.pos += 1
+            self.freed[self.accepted % self.slots].arrive(self.accepted)
         return True
 
 
-def run(n_tiles, seed, wait_freed=True):
+def run(n_tiles, seed, wait_freed=True, slots=SLOTS):
     rng = random.Random(seed)
-    ready = [Barrier(GROUPS) for _ in range(CONSUMERS)]
-    freed = [Barrier(1) for _ in range(CONSUMERS)]
-    actors = [Producer(g, n_tiles, ready, freed, wait_freed) for g in range(GROUPS)]
-    actors += [Consumer(w, n_tiles, ready, freed, rng) for w in range(CONSUMERS)]
+    ready = [Barrier(GROUPS) for _ in range(slots)]
+    freed = [Barrier(1) for _ in range(slots)]
+    queue = Queue(n_tiles)
+    actors = [Producer(g, n_tiles, ready, freed, slots, wait_freed) for g in range(GROUPS)]
+    consumers = [Consumer(w, queue, ready, freed, slots, rng) for w in range(CONSUMERS)]
+    actors += consumers
     while True:
         live = [a for a in actors if not a.done()]
         if not live:
             break
         rng.shuffle(live)
-        # producers often run ahead: give them extra turns at random
+        # producers often run ahead, filter warps run at uneven speeds: give
+        # actors extra turns at random
         moved = False
         for a in live:
-            for _ in range(1 + (rng.randrange(6) if isinstance(a, Producer) else 0)):
+            for _ in range(1 + rng.randrange(6)):
                 if a.done() or not a.step():
                     break
                 moved = True
         assert moved, "deadlock with %d tiles" % n_tiles
-    for w in range(CONSUMERS):
-        assert ready[w].phase == len(range(w, n_tiles, CONSUMERS))
-        assert ready[w].pending == 0 and freed[w].pending == 0
+    assert sorted(t for c in consumers for t in c.taken) == list(range(n_tiles))
+    for s in range(slots):
+        assert ready[s].phase == len(range(s, n_tiles, slots))
+        assert ready[s].pending == 0 and freed[s].pending == 0
 
 
-@pytest.mark.parametrize("n_tiles", [1, 2, 7, 8, 9, 16, 17, 33, 64, 193])
-def test_handover_delivers_each_tile_once_in_order(n_tiles):
+def test_queue_holds_at_least_one_slot_per_filter_warp():
+    assert SLOTS >= CONSUMERS
+
+
+@pytest.mark.parametrize("n_tiles", [1, 2, 7, 8, 9, 10, 11, 16, 17, 33, 64, 193])
+def test_handover_delivers_each_tile_once(n_tiles):
     for seed in range(40):
         run(n_tiles, seed)
 
 
 def test_handover_without_the_freed_wait_fails():
-    """The planted mistake: producers that do not wait for `freed` lap a
-    filter warp, and a parity wait then misses or misreads a phase."""
+    """Planted mistake: producers that do not wait for `freed` lap a filter
+    warp, and a parity wait then misses or misreads a phase."""
     failures = 0
     for seed in range(40):
         try:
             run(64, seed, wait_freed=False)
+        except AssertionError:
+            failures += 1
+    assert failures > 0
+
+
+def test_handover_with_fewer_slots_than_filter_warps_fails():
+    """Planted mistake: with 4 slots a filter warp can take tile r before
+    tile r - 4 is packed, and its parity wait then reads the older phase."""
+    failures = 0
+    for seed in range(40):
+        try:
+            run(64, seed, slots=4)
         except AssertionError:
             failures += 1
     assert failures > 0
