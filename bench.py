@@ -269,6 +269,7 @@ def run_batched(args, dev, peak_ops):
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.batched_steps
     stages = b.timing()
+    shapes = {E: b.shape(E) for E in range(2, 13)}
     invalid = b.invalid()
     b.close()
     del d_reads, d_refs
@@ -280,6 +281,7 @@ def run_batched(args, dev, peak_ops):
                         "unsorted, stride 256, one CUDA-graph launch per batch (tuned)" % n,
             "invalid": invalid,
             "stages_ms": stages,
+            "tuned_shapes": shapes,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                          "unit": "lane-ops/s", "frac": achieved / peak_ops,
                          "scope": "whole batch step (bucketing, packing, filters, gather)",
@@ -327,6 +329,7 @@ def run_batched_uniform(args, dev, peak_ops, h_reads, h_refs):
         st = b.timing()
         stage_list.append(st)
         kernel_ms.append(st["filter_E"][E])
+    shape = b.shape(E)
     b.close()
     accepted = int(np.unpackbits(acc.cpu().numpy().view(np.uint8)).sum())
     del d_reads, d_refs
@@ -339,7 +342,7 @@ def run_batched_uniform(args, dev, peak_ops, h_reads, h_refs):
             "workload": "%d pairs m=%d E=%d (the headline's pairs), rows at stride %d, one "
                         "CUDA-graph launch per batch (tuned)" % (n, M, E, stride),
             "accepted": accepted, "stages_ms": stages,
-            "kernel": "batch_filter_kernel<%d>" % E, "kernel_ms": k_ms,
+            "kernel": "batch_filter_kernel<%d>" % E, "kernel_ms": k_ms, "tuned_shape": shape,
             "kernel_ms_runs": [round(x, 4) for x in kernel_ms],
             "roofline": {"bound": "alu", "achieved": ops / (k_ms * 1e-3), "peak": peak_ops,
                          "unit": "lane-ops/s", "frac": ops / (k_ms * 1e-3) / peak_ops,

@@ -525,10 +525,12 @@ void shouji_pipeline_destroy(shouji_pipeline *pipeline);
  * shouji_batch_tune is the autotuner.  It runs the bucketing and packing of
  * the given batch, then times every launch shape of each threshold's filter
  * kernel (CTA of 64 or 128 threads, 1-8 CTAs per SM; groups grid-strided,
- * in a contiguous range per CTA, or taken from a shared counter) and keeps
- * the fastest.  It appends them to tune_cache
- * (when not NULL) as "<gpu> <E> <threads> <ctas/SM> <schedule> <ms>" lines,
- * which shouji_batch_create reads back.  It does not write out_accept /
+ * in a contiguous range per CTA, or taken from a shared counter; 4 or, for
+ * E <= 6, 8 windows per chunk of the filter's inner loop) and keeps the
+ * fastest.  It appends them to tune_cache (when not NULL) as
+ * "<gpu> <E> <threads> <ctas/SM> <schedule> <windows> <ms>" lines, which
+ * shouji_batch_create reads back; shouji_batch_shape returns the shape a
+ * threshold's kernel runs with.  It does not write out_accept /
  * out_count: call shouji_batch_run afterwards.  It synchronizes `stream`.
  *
  * shouji_batch_destroy waits for the last run and frees everything.
@@ -567,6 +569,9 @@ shouji_status shouji_batch_run_at(shouji_batch *batch, const uint8_t *reads, uin
                                   void *stream);
 
 shouji_status shouji_batch_invalid(shouji_batch *batch, uint64_t *n_invalid);
+
+shouji_status shouji_batch_shape(shouji_batch *batch, int E, int *threads, int *ctas_per_sm,
+                                 int *schedule, int *windows);
 
 #define SHOUJI_BATCH_TIMES (5 + SHOUJI_MAX_E + 1)
 

@@ -94,6 +94,9 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_batch_run.restype = ctypes.c_int
     lib.shouji_batch_invalid.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.shouji_batch_invalid.restype = ctypes.c_int
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.shouji_batch_shape.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip]
+    lib.shouji_batch_shape.restype = ctypes.c_int
     lib.shouji_batch_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     lib.shouji_batch_timing.restype = ctypes.c_int
     lib.shouji_batch_tune.argtypes = [vp, vp, vp, u64, vp, vp, sz, vp, vp, ctypes.c_char_p, vp]
@@ -572,6 +575,14 @@ class Batch:
         return {"graph": v[0], "bucketing": v[1], "pack": v[2], "filters": v[3],
                 "finalize": v[4], "filter_E": {E: v[5 + E] for E in range(SHOUJI_MAX_E + 1)
                                                if v[5 + E] >= 0}}
+
+    def shape(self, E: int) -> dict:
+        """Launch shape of threshold E's filter kernel (defaults or tuned)."""
+        v = [ctypes.c_int(0) for _ in range(4)]
+        _check(load_library().shouji_batch_shape(self._h, E, *[ctypes.byref(x) for x in v]),
+               "shouji_batch_shape")
+        return {"threads": v[0].value, "ctas_per_sm": v[1].value, "schedule": v[2].value,
+                "windows": v[3].value}
 
     def invalid(self) -> int:
         v = ctypes.c_uint64(0)

@@ -508,7 +508,7 @@ struct shouji_batch {
     uint8_t *d_count_slot = nullptr;
     uint2 *d_pr = nullptr, *d_pt = nullptr;
     uint32_t *d_nr = nullptr, *d_nt = nullptr;
-    int threads[kMaxE], ctas_per_sm[kMaxE], schedule[kMaxE];
+    int threads[kMaxE], ctas_per_sm[kMaxE], schedule[kMaxE], u[kMaxE];
     // One graph per argument block: graph k copies block k, so a run waits
     // only for the run kArgBufs runs before it to have started.
     cudaGraph_t graph[kArgBufs] = {};
@@ -584,6 +584,7 @@ FilterParams filter_params(const shouji_batch *b)
     p.count_slot = b->d_count_slot;
     p.work = b->d_tables->work;
     p.schedule = 0;
+    p.u = 4;
     return p;
 }
 
@@ -635,10 +636,11 @@ cudaError_t enqueue_prologue(shouji_batch *b, cudaStream_t s, int k, bool timed)
 }
 
 cudaError_t enqueue_filter(shouji_batch *b, int E, int threads, int ctas_per_sm, int schedule,
-                           cudaStream_t s)
+                           int u, cudaStream_t s)
 {
     FilterParams p = filter_params(b);
     p.schedule = schedule;
+    p.u = u;
     return kBatchFilter[E](p, threads, ctas_per_sm * b->sms, s);
 }
 
@@ -658,7 +660,8 @@ cudaError_t enqueue_all(shouji_batch *b, cudaStream_t s, int k)
             return e;
         if ((e = stamp(b->t_e0[E], t)))
             return e;
-        if ((e = enqueue_filter(b, E, b->threads[E], b->ctas_per_sm[E], b->schedule[E], t)))
+        if ((e = enqueue_filter(b, E, b->threads[E], b->ctas_per_sm[E], b->schedule[E], b->u[E],
+                                t)))
             return e;
         if ((e = stamp(b->t_e1[E], t)))
             return e;
@@ -789,7 +792,7 @@ size_t batch_bytes(size_t max_pairs, uint32_t max_m, int e_min, int e_max, int w
     return b;
 }
 
-// Tuning cache: lines "<gpu> <E> <threads> <ctas_per_sm> <schedule> <ms>".
+// Tuning cache: lines "<gpu> <E> <threads> <ctas_per_sm> <schedule> <U> <ms>".
 void load_cache(shouji_batch *b, const char *path)
 {
     if (!path)
@@ -799,14 +802,15 @@ void load_cache(shouji_batch *b, const char *path)
         return;
     char gpu[128], want[128];
     device_name(want, sizeof(want), b->device);
-    int E, th, cps, sch;
+    int E, th, cps, sch, u;
     double ms;
-    while (fscanf(f, "%127s %d %d %d %d %lf", gpu, &E, &th, &cps, &sch, &ms) == 6) {
+    while (fscanf(f, "%127s %d %d %d %d %d %lf", gpu, &E, &th, &cps, &sch, &u, &ms) == 7) {
         if (strcmp(gpu, want) == 0 && E >= 0 && E < kMaxE && (th == 64 || th == 128) &&
-            cps >= 1 && cps <= 8 && sch >= 0 && sch <= 2) {
+            cps >= 1 && cps <= 8 && sch >= 0 && sch <= 2 && (u == 4 || (u == 8 && E <= kMaxE8))) {
             b->threads[E] = th;
             b->ctas_per_sm[E] = cps;
             b->schedule[E] = sch;
+            b->u[E] = u;
         }
     }
     fclose(f);
@@ -876,6 +880,7 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, i
         b->threads[E] = 128;
         b->ctas_per_sm[E] = 4;
         b->schedule[E] = 0;
+        b->u[E] = 4;
     }
     b->slots_cap = slots_capacity(max_pairs, max_m, e_min, e_max);
     b->pack_blocks_cap = b->slots_cap / kPackSeqs;
@@ -1018,6 +1023,18 @@ shouji_status shouji_batch_run_at(shouji_batch *b, const uint8_t *reads, uint64_
                      out_accept, out_count, stream);
 }
 
+shouji_status shouji_batch_shape(shouji_batch *b, int E, int *threads, int *ctas_per_sm,
+                                 int *schedule, int *windows)
+{
+    if (!b || E < 0 || E >= kMaxE || !threads || !ctas_per_sm || !schedule || !windows)
+        return SHOUJI_EINVAL;
+    *threads = b->threads[E];
+    *ctas_per_sm = b->ctas_per_sm[E];
+    *schedule = b->schedule[E];
+    *windows = b->u[E];
+    return SHOUJI_OK;
+}
+
 shouji_status shouji_batch_timing(shouji_batch *b, float *ms, int n)
 {
     if (!b || !ms || n < SHOUJI_BATCH_TIMES)
@@ -1082,15 +1099,8 @@ shouji_status shouji_batch_tune(shouji_batch *b, const uint8_t *reads, const uin
     if ((e = cudaMemcpy(groups, b->d_tables->ec_groups, sizeof(groups), cudaMemcpyDeviceToHost)))
         return cuda_status(e);
     struct Cand {
-        int th, cps, sch;
+        int th, cps, sch, u;
     };
-    std::vector<Cand> cands;
-    for (int sch = 0; sch < 3; ++sch) {
-        for (int cps : {1, 2, 3, 4})
-            cands.push_back({128, cps, sch});
-        for (int cps : {2, 4, 6, 8})
-            cands.push_back({64, cps, sch});
-    }
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
@@ -1100,12 +1110,24 @@ shouji_status shouji_batch_tune(shouji_batch *b, const uint8_t *reads, const uin
     for (int E = b->e_lo; E <= b->e_hi && !e; ++E) {
         if (!groups[E])
             continue;
+        // launch shapes x schedules x windows per chunk
+        std::vector<Cand> cands;
+        for (int u : {4, 8}) {
+            if (u == 8 && E > kMaxE8)
+                continue;
+            for (int sch = 0; sch < 3; ++sch) {
+                for (int cps : {1, 2, 3, 4})
+                    cands.push_back({128, cps, sch, u});
+                for (int cps : {2, 4, 6, 8})
+                    cands.push_back({64, cps, sch, u});
+            }
+        }
         float best = 1e30f;
-        Cand pick = {b->threads[E], b->ctas_per_sm[E], b->schedule[E]};
+        Cand pick = {b->threads[E], b->ctas_per_sm[E], b->schedule[E], b->u[E]};
         for (const Cand &c : cands) {
             auto once = [&]() -> cudaError_t {
                 cudaError_t r = cudaMemsetAsync(b->d_tables->work, 0, sizeof(uint32_t) * kMaxE, s);
-                return r ? r : enqueue_filter(b, E, c.th, c.cps, c.sch, s);
+                return r ? r : enqueue_filter(b, E, c.th, c.cps, c.sch, c.u, s);
             };
             if ((e = once()))  // warm-up
                 break;
@@ -1116,7 +1138,7 @@ shouji_status shouji_batch_tune(shouji_batch *b, const uint8_t *reads, const uin
                 if ((e = cudaMemsetAsync(b->d_tables->work, 0, sizeof(uint32_t) * kMaxE, s)))
                     break;
                 cudaEventRecord(t0, s);
-                if ((e = enqueue_filter(b, E, c.th, c.cps, c.sch, s)))
+                if ((e = enqueue_filter(b, E, c.th, c.cps, c.sch, c.u, s)))
                     break;
                 cudaEventRecord(t1, s);
                 if ((e = cudaEventSynchronize(t1)))
@@ -1138,8 +1160,10 @@ shouji_status shouji_batch_tune(shouji_batch *b, const uint8_t *reads, const uin
         b->threads[E] = pick.th;
         b->ctas_per_sm[E] = pick.cps;
         b->schedule[E] = pick.sch;
+        b->u[E] = pick.u;
         if (f)
-            fprintf(f, "%s %d %d %d %d %.6f\n", gpu, E, pick.th, pick.cps, pick.sch, best);
+            fprintf(f, "%s %d %d %d %d %d %.6f\n", gpu, E, pick.th, pick.cps, pick.sch, pick.u,
+                    best);
     }
     if (f)
         fclose(f);

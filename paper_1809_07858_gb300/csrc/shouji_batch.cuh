@@ -21,6 +21,10 @@ constexpr int kMaxE = 32;             // thresholds 0..31
 constexpr int kBins = kMaxM * kMaxE;  // bucket key = m * 32 + E
 constexpr uint16_t kBadKey = 0xFFFF;
 constexpr uint32_t kNoPair = 0xFFFFFFFFu;
+// Windows per chunk of the filter's loop that the tuner may choose per
+// threshold: 4 always, 8 for thresholds up to kMaxE8 (the longer chunk keeps
+// about twice the map columns live; above that its registers grow past 200).
+constexpr int kMaxE8 = 6;
 
 // Per-run arguments, read by every kernel from device memory (the CUDA graph
 // copies them from a pinned host block at the start of each launch).
@@ -63,6 +67,7 @@ struct FilterParams {
     int schedule;                    // 0: grid-strided groups; 1: a contiguous range per
                                      // CTA; 2: CTAs take blockDim groups at a time from a
                                      // shared counter
+    int u;                           // windows per chunk: 4, or 8 for small thresholds
 };
 
 template <int E>

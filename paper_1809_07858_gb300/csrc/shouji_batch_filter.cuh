@@ -11,7 +11,7 @@
 namespace shouji {
 namespace batch {
 
-template <int E, bool WITH_N>
+template <int E, int U, bool WITH_N>
 __global__ void __launch_bounds__(filt::kThreads, filt::min_blocks<E>())
 batch_filter_kernel(FilterParams p)
 {
@@ -66,7 +66,7 @@ batch_filter_kernel(FilterParams p)
         for (int j = 0; j <= E; ++j)
             inactive[j] = 0u;
         uint32_t C[8];
-        filt::filter_group<E, SHOUJI_FILTER_U, WITH_N ? 1 : 0>(v, inactive, C);
+        filt::filter_group<E, U, WITH_N ? 1 : 0>(v, inactive, C);
         uint32_t cw[8];
         filt::counts_to_bytes(C, cw);
         uint4 *dst = reinterpret_cast<uint4 *>(p.count_slot + slot0);
@@ -108,10 +108,19 @@ batch_filter_kernel(FilterParams p)
 template <int E>
 cudaError_t launch_filter_E(const FilterParams &p, int threads, int ctas, cudaStream_t s)
 {
+    if constexpr (E <= kMaxE8) {
+        if (p.u == 8) {
+            if (p.nreads)
+                batch_filter_kernel<E, 8, true><<<ctas, threads, 0, s>>>(p);
+            else
+                batch_filter_kernel<E, 8, false><<<ctas, threads, 0, s>>>(p);
+            return cudaGetLastError();
+        }
+    }
     if (p.nreads)
-        batch_filter_kernel<E, true><<<ctas, threads, 0, s>>>(p);
+        batch_filter_kernel<E, SHOUJI_FILTER_U, true><<<ctas, threads, 0, s>>>(p);
     else
-        batch_filter_kernel<E, false><<<ctas, threads, 0, s>>>(p);
+        batch_filter_kernel<E, SHOUJI_FILTER_U, false><<<ctas, threads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

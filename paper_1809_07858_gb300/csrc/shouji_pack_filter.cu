@@ -18,7 +18,7 @@
 //  - 8 consumer warps filter the tiles already packed; a consumer that is
 //    done with a tile takes the next one from a counter in shared memory, so
 //    the tiles go to whichever consumer is free.
-// Tiles go through a queue of kSlots slots: tile r of the CTA's range uses
+// Tiles go through a queue of kSlots (12) slots: tile r of the CTA's range uses
 // slot r % kSlots, whose two mbarriers hand it over: `ready` (all 512
 // producer threads arrive once their words of the tile are written) and
 // `freed` (the consumer's 32 threads arrive once they have filtered it).
@@ -54,7 +54,7 @@ using namespace packdev;
 
 constexpr int kConsumers = 8;                      // filter warps per CTA
 #ifndef SHOUJI_FUSED_SLOTS
-#define SHOUJI_FUSED_SLOTS 10
+#define SHOUJI_FUSED_SLOTS 12
 #endif
 constexpr int kSlots = SHOUJI_FUSED_SLOTS;         // tiles in flight per CTA
 static_assert(kSlots >= kConsumers, "a consumer's wait needs the slot's previous phase done");

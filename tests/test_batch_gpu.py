@@ -120,14 +120,38 @@ def test_tuned_shapes_give_identical_results(tmp_path):
     acc1, cnt1 = b.run(*args)
     torch.cuda.synchronize()
     assert torch.equal(acc0, acc1.cpu()) and torch.equal(cnt0, cnt1.cpu())
-    lines = open(cache).read().split("\n")
-    assert sum(1 for l in lines if l.strip()) == 11     # E = 2..12 present in the batch
+    lines = [l.split() for l in open(cache).read().split("\n") if l.strip()]
+    assert len(lines) == 11     # E = 2..12 present in the batch
     b2 = sj.Batch(40_000, 255, 2, 12, tune_cache=cache)   # reads the cache back
+    for f in lines:
+        E = int(f[1])
+        want = {"threads": int(f[2]), "ctas_per_sm": int(f[3]), "schedule": int(f[4]),
+                "windows": int(f[5])}
+        assert b.shape(E) == want and b2.shape(E) == want
+        assert want["windows"] in (4, 8) and (want["windows"] == 4 or E <= 6)
     acc2, cnt2 = b2.run(*args)
     torch.cuda.synchronize()
     assert torch.equal(acc0, acc2.cpu()) and torch.equal(cnt0, cnt2.cpu())
     b.close()
     b2.close()
+
+
+@pytest.mark.parametrize("with_n", [False, True])
+def test_eight_windows_per_chunk_bit_exact(tmp_path, with_n):
+    """The filter kernels with 8 windows per chunk (thresholds up to 6),
+    forced through a tuning cache, against the oracle."""
+    reads, refs, lens, Es = mixed_batch(30_000, seed=8, n_rate=0.002 if with_n else 0.0,
+                                        choices=(1, 7, 33, 100, 150, 255),
+                                        weights=(0.05, 0.1, 0.15, 0.3, 0.3, 0.1), e_range=(0, 6))
+    cache = tmp_path / "u8.txt"
+    gpu = torch.cuda.get_device_name(0).replace(" ", "_")
+    cache.write_text("".join("%s %d 64 4 2 8 1.0\n" % (gpu, E) for E in range(0, 7)))
+    b = sj.Batch(30_000, 255, 0, 6, with_n=with_n, tune_cache=str(cache))
+    assert all(b.shape(E)["windows"] == 8 for E in range(0, 7))
+    acc, cnt = run_batch(b, reads, refs, lens, Es)
+    acc_o, cnt_o = oracle_mixed(reads, refs, lens, Es)
+    assert (cnt == cnt_o).all() and (acc == acc_o).all()
+    b.close()
 
 
 def test_runs_queued_back_to_back_use_their_own_arguments():

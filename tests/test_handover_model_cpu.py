@@ -120,7 +120,7 @@ class Consumer:
         return True
 
 
-def run(n_tiles, seed, wait_freed=True, slots=SLOTS):
+def run(n_tiles, seed, wait_freed=True, slots=SLOTS, producer_turns=6):
     rng = random.Random(seed)
     ready = [Barrier(GROUPS) for _ in range(slots)]
     freed = [Barrier(1) for _ in range(slots)]
@@ -137,7 +137,8 @@ def run(n_tiles, seed, wait_freed=True, slots=SLOTS):
         # actors extra turns at random
         moved = False
         for a in live:
-            for _ in range(1 + rng.randrange(6)):
+            turns = producer_turns if isinstance(a, Producer) else 6
+            for _ in range(1 + rng.randrange(turns)):
                 if a.done() or not a.step():
                     break
                 moved = True
@@ -164,7 +165,8 @@ def test_handover_without_the_freed_wait_fails():
     failures = 0
     for seed in range(40):
         try:
-            run(64, seed, wait_freed=False)
+            # producers far faster than the filter warps, so that they lap them
+            run(64, seed, wait_freed=False, producer_turns=200)
         except AssertionError:
             failures += 1
     assert failures > 0
