@@ -323,11 +323,27 @@ struct PackBlock {
     uint32_t slot0, rel, mc;
 };
 
+// Rows left free after each lane's 32 staged rows of length m in the
+// persistent pack: with them the lanes of a warp read distinct banks with the
+// rows in order (pack_transpose_spaced).  They are used only where a buffer
+// of buf_bytes holds them; otherwise (0) the rows are staged densely and
+// read in a rotated order (pack_transpose).
+__host__ __device__ inline int lane_gap(int m, int buf_bytes)
+{
+    const int gap = packdev::rotation_step(row_stride(m), kPackLanes);
+    const int fits = (kPackSeqs + (kPackLanes - 1) * gap) * row_stride(m) + 16 <= buf_bytes;
+    return fits ? gap : 0;
+}
+
 // m-class tables of a run, copied to shared memory by the persistent pack.
 struct McCache {
     uint32_t n_mc, total;
-    uint32_t block[kMaxM + 1], m[kMaxM], slot[kMaxM];
+    uint32_t block[kMaxM + 1], slot[kMaxM];
+    uint16_t m[kMaxM];
     uint64_t poff[kMaxM];
+    // rows left free after each lane's 32 staged rows (0: rows staged densely
+    // and read in a rotated order instead), and that rotation step
+    uint8_t gap[kMaxM], rot[kMaxM];
 };
 
 __device__ __forceinline__ PackBlock locate_block(const McCache &c, uint32_t blk)
@@ -382,6 +398,8 @@ pack_async_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int 
         mc.m[i] = T->mc_m[i];
         mc.slot[i] = T->mc_slot[i];
         mc.poff[i] = T->mc_poff[i];
+        mc.gap[i] = (uint8_t)lane_gap((int)T->mc_m[i], buf_bytes);
+        mc.rot[i] = (uint8_t)packdev::rotation_step(row_stride((int)T->mc_m[i]), kPackLanes);
     }
     __syncthreads();
 
@@ -399,13 +417,15 @@ pack_async_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int 
         if (blk < total) {
             const PackBlock b = locate_block(mc, blk);
             const int nck = (b.m + 15) >> 4;
+            const int gap = mc.gap[b.mc];
             const uint32_t *pk = P[k % 3];
             for (int it = threadIdx.x; it < kPackSeqs * nck; it += kPackThreads) {
                 const int r = it / nck, c = it - r * nck;
                 const uint32_t pair = pk[r];
                 const bool ok = pair != kNoPair;
                 const uint8_t *src = ok ? seqs + (uint64_t)pair * stride + 16 * c : seqs;
-                cp_async16(dst + r * b.rs + 16 * c, src, ok ? 16u : 0u);
+                // row r of lane r / 32 goes to staged row r + (r / 32) * gap
+                cp_async16(dst + (r + (r >> 5) * gap) * b.rs + 16 * c, src, ok ? 16u : 0u);
             }
         }
         cp_async_commit();  // an empty group past the last block keeps the count regular
@@ -426,9 +446,14 @@ pack_async_kernel(const Args *__restrict__ a, const Tables *__restrict__ T, int 
         const int lane0 = (int)((b.rel % kTile) / 32);
         uint32_t *packed = reinterpret_cast<uint32_t *>((blockIdx.y ? prefs : preads) + mc.poff[b.mc]);
         uint32_t *nmask = WITH_N ? (blockIdx.y ? nrefs : nreads) + mc.poff[b.mc] : nullptr;
-        const uint32_t seen = packdev::pack_transpose<WITH_N, true, kPackLanes>(
-            reinterpret_cast<const uint32_t *>((k & 1) ? buf1 : buf0), b.m, b.rs, tile, lane0,
-            packed, nmask, packdev::rotation_step(b.rs, kPackLanes), kPackThreads);
+        const uint32_t *sbuf = reinterpret_cast<const uint32_t *>((k & 1) ? buf1 : buf0);
+        const uint32_t seen =
+            mc.gap[b.mc] ? packdev::pack_transpose_spaced<WITH_N, kPackLanes>(
+                               sbuf, b.m, b.rs, mc.gap[b.mc], tile, lane0, packed, nmask,
+                               kPackThreads, (int)threadIdx.x)
+                         : packdev::pack_transpose<WITH_N, true, kPackLanes>(
+                               sbuf, b.m, b.rs, tile, lane0, packed, nmask, mc.rot[b.mc],
+                               kPackThreads);
         P[(k + 2) % 3][threadIdx.x] = ahead;
         // the buffer of block k is refilled in step k+1, after this barrier
         if (WITH_N)
@@ -571,6 +596,20 @@ size_t pack_smem(uint32_t max_m)
         best = b > best ? b : best;
     }
     return best;
+}
+
+// Bytes of one buffer of the persistent pack that stages every length up to
+// max_m with its lane gaps.
+size_t async_smem_spaced(uint32_t max_m)
+{
+    size_t best = 0;
+    for (uint32_t m = 1; m <= max_m; ++m) {
+        const size_t b = (size_t)(kPackSeqs + (kPackLanes - 1) *
+                                  packdev::rotation_step(row_stride((int)m), kPackLanes)) *
+                             row_stride((int)m) + 16;
+        best = b > best ? b : best;
+    }
+    return (best + 15) / 16 * 16;
 }
 
 FilterParams filter_params(const shouji_batch *b)
@@ -923,22 +962,39 @@ shouji_status shouji_batch_create(size_t max_pairs, uint32_t max_m, int e_min, i
                              cudaSharedmemCarveoutMaxShared);
     }
     if (ok) {
-        // persistent pack: as many CTAs per side as fit on the GPU at once
-        b->async_buf = (int)((pack_smem(max_m) + 15) / 16 * 16);
-        const size_t asmem = 2 * (size_t)b->async_buf;
-        ok = cudaFuncSetAttribute(pack_async_kernel<true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem) == cudaSuccess &&
-             cudaFuncSetAttribute(pack_async_kernel<false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem) == cudaSuccess;
-        cudaFuncSetAttribute(pack_async_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(pack_async_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+        // persistent pack: buffers that hold every length with its lane gaps
+        // while at least 3 CTAs fit on an SM, else buffers of dense rows
+        // (the lengths whose gaps do not fit are read in a rotated order);
+        // as many CTAs per side as fit on the GPU at once
+        const size_t dense = (pack_smem(max_m) + 15) / 16 * 16;
+        const size_t spaced = async_smem_spaced(max_m);
+        auto fit = [&](size_t buf, int *per_sm) -> bool {
+            const size_t asmem = 2 * buf;
+            bool good = cudaFuncSetAttribute(pack_async_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)asmem) == cudaSuccess &&
+                        cudaFuncSetAttribute(pack_async_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)asmem) == cudaSuccess;
+            cudaFuncSetAttribute(pack_async_kernel<true>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+            cudaFuncSetAttribute(pack_async_kernel<false>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+            *per_sm = 0;
+            return good && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               per_sm, with_n ? pack_async_kernel<true> : pack_async_kernel<false>,
+                               kPackThreads, asmem) == cudaSuccess;
+        };
         int per_sm = 0;
-        if (ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                      &per_sm, with_n ? pack_async_kernel<true> : pack_async_kernel<false>,
-                      kPackThreads, asmem) != cudaSuccess)
-            ok = false;
+        b->async_buf = (int)spaced;
+        ok = fit(spaced, &per_sm);
+        if (!ok || per_sm < 3) {
+            cudaGetLastError();
+            b->async_buf = (int)dense;
+            ok = fit(dense, &per_sm);
+        }
         b->async_grid = per_sm > 1 ? per_sm * b->sms / 2 : b->sms;
     }
     if (ok && pack_smem(max_m) > 48 * 1024) {

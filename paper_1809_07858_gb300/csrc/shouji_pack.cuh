@@ -164,6 +164,71 @@ __device__ __forceinline__ uint32_t pack_transpose_w_odd(const uint32_t *__restr
     return seen;
 }
 
+// pack_transpose_by for staged rows laid out so that no rotation is needed:
+// the 32 rows of lane l of the block start at row l * (32 + gap) (a gap of
+// `gap` rows after each lane), with gap * (rs / 4) = 32 / LANES (mod 32)
+// (rotation_step), so that at every step the LANES lanes of a warp read
+// banks 32 / LANES apart.  A thread owns (lane, 4 consecutive positions) and
+// reads its lane's rows in order, one pointer step per row, so each base
+// costs a shift and a mask-and-or per plane and no address arithmetic; the
+// output words need no rotation.  Requires rs % 4 == 0.  Without WITH_N,
+// returns the OR of the bases read (bytes past the end of a row left out).
+template <bool WITH_N, int LANES>
+__device__ __forceinline__ uint32_t pack_transpose_spaced(const uint32_t *__restrict__ sm, int m,
+                                                          int rs, int gap, size_t tile,
+                                                          int lane0,
+                                                          uint32_t *__restrict__ packed,
+                                                          uint32_t *__restrict__ nmask,
+                                                          int nthreads, int tid)
+{
+    const int J = (m + 3) >> 2;
+    const int ws = rs >> 2;  // words per staged row
+    uint32_t seen = 0;
+    for (int item = tid; item < LANES * J; item += nthreads) {
+        const int l = item % LANES, j = item / LANES;
+        const uint32_t keep = 4 * j + 4 <= m ? ~0u : (1u << (8 * (m - 4 * j))) - 1u;
+        const uint32_t *row = sm + l * (32 + gap) * ws + j;  // word j of the lane's row 0
+        uint32_t yh[4], yl[4], yn[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            uint32_t h = 0, lo = 0, nn = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t w = *row;
+                row += ws;
+                const uint32_t xh = u >= 2 ? w << (u - 2) : w >> (2 - u);
+                const uint32_t xl = u >= 1 ? w << (u - 1) : w >> 1;
+                h |= xh & (0x01010101u << u);
+                lo |= xl & (0x01010101u << u);
+                if (WITH_N)
+                    nn |= (n_bytes(w) >> 7) << u;
+                else
+                    seen |= w & keep;
+            }
+            yh[t] = h;
+            yl[t] = lo;
+            yn[t] = nn;
+        }
+        uint32_t H[4], L[4], N[4];
+        transpose4x4(yh[0], yh[1], yh[2], yh[3], H);
+        transpose4x4(yl[0], yl[1], yl[2], yl[3], L);
+        if (WITH_N)
+            transpose4x4(yn[0], yn[1], yn[2], yn[3], N);
+        const int lane = lane0 + l;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int p = 4 * j + q;
+            if (p < m) {
+                const size_t wi = (tile * (size_t)m + p) * 32 + lane;
+                reinterpret_cast<uint2 *>(packed)[wi] = make_uint2(H[q], L[q]);
+                if (WITH_N)
+                    nmask[wi] = N[q];
+            }
+        }
+    }
+    return seen;
+}
+
 // pack_transpose_by with the threads of the CTA in threadIdx.x order.
 template <bool WITH_N, bool ALIGNED, int LANES = 8>
 __device__ __forceinline__ uint32_t pack_transpose(const uint32_t *__restrict__ sm, int m, int rs,

@@ -114,3 +114,49 @@ def test_rotated_transposition_reads_32_banks(m):
     c = rotation_step(m)
     for banks in warp_banks(m, lambda l: general_rows(l, c), m // 4):
         assert len(banks) == 32, m
+
+
+# The batched form's persistent pack (csrc/shouji_batch.cu, pack_async_kernel)
+# stages 128 rows (4 lanes) at a row stride of m rounded up to 16 bytes (and
+# off multiples of 32), leaving `gap` free rows after each lane's 32 rows, and
+# pack_transpose_spaced reads each lane's rows in order.
+
+BATCH_SEQS, BATCH_LANES = 128, 4
+
+
+def batch_row_stride(m):
+    rs = (m + 15) & ~15
+    return rs + 16 if rs % 32 == 0 else rs
+
+
+def lane_gap(m):
+    return rotation_step(batch_row_stride(m), BATCH_LANES)
+
+
+def spaced_word(l, k, j, m):
+    """Shared-memory word that lane l's item of quad j reads at step k."""
+    ws = batch_row_stride(m) // 4
+    return (l * (32 + lane_gap(m)) + k) * ws + j
+
+
+@pytest.mark.parametrize("m", range(1, 256))
+def test_spaced_rows_read_32_distinct_banks_and_stay_in_the_buffer(m):
+    rs, gap = batch_row_stride(m), lane_gap(m)
+    assert gap in (2, 6)  # the step exists for every staged row stride
+    # the smallest buffer that holds length m with its gaps (the kernel uses
+    # gaps only when its buffer is at least this large)
+    buf_words = ((BATCH_SEQS + (BATCH_LANES - 1) * gap) * rs + 16) // 4
+    J = (m + 3) // 4
+    its = [(item % BATCH_LANES, item // BATCH_LANES) for item in range(BATCH_LANES * J)]
+    for w0 in range(0, len(its), 32):
+        warp = its[w0:w0 + 32]
+        for k in range(32):
+            banks = [spaced_word(l, k, j, m) % 32 for l, j in warp]
+            assert len(set(banks)) == len(banks), (m, w0, k)
+    for l, j in its:
+        for k in range(32):
+            assert 0 <= spaced_word(l, k, j, m) < buf_words
+    # every staged row (where the copies put it) is a row the lanes read
+    staged = {r + (r // 32) * gap for r in range(BATCH_SEQS)}
+    read = {l * (32 + gap) + k for l in range(BATCH_LANES) for k in range(32)}
+    assert staged == read
