@@ -735,8 +735,35 @@ def run_ours(args, world, rank, local):
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    pipe.close()
     assert e2e_acc == n_accepted, (e2e_acc, n_accepted)
+
+    # The same through shouji_pipeline_run_packed, for callers that keep their
+    # pairs in the packed 2-bit layout (a quarter of the ASCII bytes): the
+    # packed words written above by shouji_pack, copied to pinned host memory
+    # before the timed region.
+    hp_r = torch.empty(packed_r.numel(), dtype=torch.int32, pin_memory=True)
+    hp_t = torch.empty_like(hp_r, pin_memory=True)
+    hp_r.copy_(packed_r)
+    hp_t.copy_(packed_t)
+    for _ in range(2):
+        pipe.run_packed(hp_r, hp_t, n, E, h_acc, count=h_cnt, idx=h_idx)
+    barrier()
+    e2e_packed_ms = []
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        t1 = time.perf_counter()
+        packed_acc = pipe.run_packed(hp_r, hp_t, n, E, h_acc, count=h_cnt, idx=h_idx)
+        e2e_packed_ms.append(round(1000 * (time.perf_counter() - t1), 2))
+    e2e_packed_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_packed_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_packed_s = float(t.item())
+    pipe.close()
+    assert packed_acc == n_accepted, (packed_acc, n_accepted)
+    packed_h2d = 2 * hp_r.numel() * 4
+    del hp_r, hp_t
 
     if rank != 0:
         return 0
@@ -826,6 +853,12 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "step_ms": e2e_steps_ms,
                 "path": "shouji_pipeline_run, pinned host buffers, chunks of %d pairs" % args.chunk},
+        "e2e_packed_input": {
+            "value": world * n * args.e2e_steps / e2e_packed_s, "unit": UNIT,
+            "h2d_bytes_per_step": packed_h2d, "d2h_bytes_per_step": d2h,
+            "steps": args.e2e_steps, "step_ms": e2e_packed_ms,
+            "path": "shouji_pipeline_run_packed, pairs held in pinned host memory in the "
+                    "packed 2-bit layout, chunks of %d pairs" % args.chunk},
         "gpu_launches": (4 if fused else 6) * args.steps,
         "roofline": roofline,
         "alu_peak": alu,

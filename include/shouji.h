@@ -467,6 +467,27 @@ shouji_status shouji_pipeline_run(shouji_pipeline *pipeline,
                                   uint32_t *accept, uint8_t *count,
                                   uint32_t *idx, uint64_t *n_accepted);
 
+/*
+ * shouji_pipeline_run_packed is shouji_pipeline_run for pairs that the
+ * caller holds in the packed layout described at the top of this header
+ * (for example written by shouji_pack and kept): the copies carry 2 bits per
+ * base instead of 8, and no pack runs on the device.
+ *   reads, refs      host uint32[shouji_packed_words(n_pairs, m)] each.
+ *   reads_n, refs_n  host uint32[shouji_nmask_words(n_pairs, m)] each: the N
+ *                    masks, or both NULL (no base is 'N').  Masks need a
+ *                    pipeline created with with_n.
+ *   the rest         as for shouji_pipeline_run.
+ * Errors: SHOUJI_EINVAL (bad argument, only one mask, masks without with_n;
+ * nothing launched), SHOUJI_ECUDA.  Bits past n_pairs in the last tile are
+ * read but their results are not returned.
+ */
+shouji_status shouji_pipeline_run_packed(shouji_pipeline *pipeline,
+                                         const uint32_t *reads, const uint32_t *refs,
+                                         const uint32_t *reads_n, const uint32_t *refs_n,
+                                         size_t n_pairs, int E, uint32_t *accept,
+                                         uint8_t *count, uint32_t *idx,
+                                         uint64_t *n_accepted);
+
 void shouji_pipeline_destroy(shouji_pipeline *pipeline);
 
 /*

@@ -136,6 +136,9 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_pipeline_run.argtypes = [vp, vp, vp, u64, sz, ctypes.c_int, vp, vp, vp,
                                         ctypes.POINTER(ctypes.c_uint64)]
     lib.shouji_pipeline_run.restype = ctypes.c_int
+    lib.shouji_pipeline_run_packed.argtypes = [vp, vp, vp, vp, vp, sz, ctypes.c_int, vp, vp, vp,
+                                               ctypes.POINTER(ctypes.c_uint64)]
+    lib.shouji_pipeline_run_packed.restype = ctypes.c_int
     lib.shouji_pipeline_destroy.argtypes = [vp]
     lib.shouji_pipeline_destroy.restype = None
     _lib = lib
@@ -485,6 +488,18 @@ class Pipeline:
             self._h, _host_ptr(reads), _host_ptr(refs), self.m if stride is None else stride,
             n_pairs, E, _host_ptr(accept), _host_ptr(count), _host_ptr(idx),
             ctypes.byref(n_acc)), "shouji_pipeline_run")
+        return n_acc.value
+
+    def run_packed(self, reads, refs, n_pairs: int, E: int, accept, *, reads_n=None,
+                   refs_n=None, count=None, idx=None) -> int:
+        """The same for pairs already in the packed layout (host uint32
+        arrays of ``shouji_packed_words(n_pairs, m)`` words; N masks of
+        ``shouji_nmask_words(n_pairs, m)`` words, or None)."""
+        n_acc = ctypes.c_uint64(0)
+        _check(load_library().shouji_pipeline_run_packed(
+            self._h, _host_ptr(reads), _host_ptr(refs), _host_ptr(reads_n), _host_ptr(refs_n),
+            n_pairs, E, _host_ptr(accept), _host_ptr(count), _host_ptr(idx),
+            ctypes.byref(n_acc)), "shouji_pipeline_run_packed")
         return n_acc.value
 
     def close(self):

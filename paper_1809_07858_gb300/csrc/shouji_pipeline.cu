@@ -8,6 +8,9 @@
 // the previous one:
 //   H2D reads, refs -> shouji_pack x2 -> shouji_filter -> D2H accept (+count)
 //                                                     -> compaction (+indices)
+// shouji_pipeline_run_packed takes pairs the caller already holds in the
+// packed 2-bit layout (2 bits per base instead of 8), copies those words and
+// filters them, so that it moves a quarter of the bytes over the host link.
 // Survivor indices of successive chunks are appended to one device array in
 // input order (the compaction of chunk k waits for that of chunk k-1 through
 // an event, and carries the running total on the device), and copied back
@@ -145,23 +148,28 @@ shouji_status shouji_pipeline_create(uint32_t m, size_t chunk_pairs, size_t max_
 
 void shouji_pipeline_destroy(shouji_pipeline *p) { release(p); }
 
-shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, const uint8_t *refs,
-                                  uint64_t stride, size_t n_pairs, int E, uint32_t *accept,
-                                  uint8_t *count, uint32_t *idx, uint64_t *n_accepted)
+}  // extern "C"
+
+namespace {
+
+// Runs a batch chunk by chunk on the two streams.  stage(slot, base, nc, s,
+// args) enqueues on stream s whatever puts the nc pairs from pair `base` on
+// the device in the packed layout (the slot's buffers), and sets the
+// filter's input pointers in args; the filter, the copies back and the
+// compaction follow.  check_n: report an 'N' read without N masks.
+template <class Stage>
+shouji_status run_chunks(shouji_pipeline *p, size_t n_pairs, int E, uint32_t *accept,
+                         uint8_t *count, uint32_t *idx, uint64_t *n_accepted, bool check_n,
+                         Stage stage)
 {
-    if (!p || E < 0 || E > SHOUJI_MAX_E || stride < p->m)
-        return SHOUJI_EINVAL;
     if (n_pairs == 0) {
         if (n_accepted)
             *n_accepted = 0;
         return SHOUJI_OK;
     }
-    if (!reads || !refs || !accept)
-        return SHOUJI_EINVAL;
     if (idx && n_pairs > p->max_pairs)
         return SHOUJI_EINVAL;
     DeviceGuard g(p->device);
-    const uint32_t m = p->m;
     const bool want_idx = idx != nullptr;
     cudaError_t e = cudaSuccess;
 #define SHOUJI_TRY(x)                          \
@@ -180,32 +188,14 @@ shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, cons
     for (size_t base = 0; base < n_pairs; base += p->chunk, slot ^= 1) {
         cudaStream_t s = p->st[slot];
         const size_t nc = (n_pairs - base < p->chunk) ? n_pairs - base : p->chunk;
-        if (stride == m) {
-            SHOUJI_TRY(cudaMemcpyAsync(p->d_reads[slot], reads + base * m, nc * m,
-                                       cudaMemcpyHostToDevice, s));
-            SHOUJI_TRY(cudaMemcpyAsync(p->d_refs[slot], refs + base * m, nc * m,
-                                       cudaMemcpyHostToDevice, s));
-        } else {
-            SHOUJI_TRY(cudaMemcpy2DAsync(p->d_reads[slot], m, reads + base * stride, stride, m,
-                                         nc, cudaMemcpyHostToDevice, s));
-            SHOUJI_TRY(cudaMemcpy2DAsync(p->d_refs[slot], m, refs + base * stride, stride, m,
-                                         nc, cudaMemcpyHostToDevice, s));
-        }
-        SHOUJI_TRY(launch_pack(p->d_reads[slot], m, nc, (int)m, p->d_pr[slot],
-                               p->with_n ? p->d_nr[slot] : nullptr, s, p->d_nflag + slot));
-        SHOUJI_TRY(launch_pack(p->d_refs[slot], m, nc, (int)m, p->d_pt[slot],
-                               p->with_n ? p->d_nt[slot] : nullptr, s, p->d_nflag + slot));
         FilterArgs a;
-        a.reads = reinterpret_cast<const uint2 *>(p->d_pr[slot]);
-        a.refs = reinterpret_cast<const uint2 *>(p->d_pt[slot]);
-        a.reads_n = p->with_n ? p->d_nr[slot] : nullptr;
-        a.refs_n = p->with_n ? p->d_nt[slot] : nullptr;
+        SHOUJI_TRY(stage(slot, base, nc, s, a));
         a.E_per_pair = nullptr;
         a.accept = p->d_acc[slot];
         a.count = count ? p->d_cnt[slot] : nullptr;
         a.vectors = nullptr;
         a.n_pairs = nc;
-        a.m = (int)m;
+        a.m = (int)p->m;
         SHOUJI_TRY(launch_filter(a, E, s));
         SHOUJI_TRY(cudaMemcpyAsync(accept + base / 32, p->d_acc[slot], groups_of(nc) * 4,
                                    cudaMemcpyDeviceToHost, s));
@@ -236,7 +226,7 @@ shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, cons
             total += (uint64_t)__builtin_popcount(accept[w]);
     }
     unsigned int nflag[2] = {0, 0};
-    if (!p->with_n)
+    if (check_n)
         SHOUJI_TRY(cudaMemcpy(nflag, p->d_nflag, sizeof nflag, cudaMemcpyDeviceToHost));
     const bool unmasked_n = nflag[0] || nflag[1];
 #undef SHOUJI_TRY
@@ -244,6 +234,87 @@ shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, cons
         *n_accepted = total;
     // Results are complete either way; without N masks an 'N' was read as 'G'.
     return unmasked_n ? SHOUJI_EINVAL : SHOUJI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+shouji_status shouji_pipeline_run(shouji_pipeline *p, const uint8_t *reads, const uint8_t *refs,
+                                  uint64_t stride, size_t n_pairs, int E, uint32_t *accept,
+                                  uint8_t *count, uint32_t *idx, uint64_t *n_accepted)
+{
+    if (!p || E < 0 || E > SHOUJI_MAX_E || stride < p->m)
+        return SHOUJI_EINVAL;
+    if (n_pairs && (!reads || !refs || !accept))
+        return SHOUJI_EINVAL;
+    const uint32_t m = p->m;
+    auto stage = [&](int slot, size_t base, size_t nc, cudaStream_t s, FilterArgs &a) {
+        cudaError_t e;
+        if (stride == m) {
+            e = cudaMemcpyAsync(p->d_reads[slot], reads + base * m, nc * m,
+                                cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(p->d_refs[slot], refs + base * m, nc * m,
+                                    cudaMemcpyHostToDevice, s);
+        } else {
+            e = cudaMemcpy2DAsync(p->d_reads[slot], m, reads + base * stride, stride, m, nc,
+                                  cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(p->d_refs[slot], m, refs + base * stride, stride, m, nc,
+                                      cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess)
+            e = launch_pack(p->d_reads[slot], m, nc, (int)m, p->d_pr[slot],
+                            p->with_n ? p->d_nr[slot] : nullptr, s, p->d_nflag + slot);
+        if (e == cudaSuccess)
+            e = launch_pack(p->d_refs[slot], m, nc, (int)m, p->d_pt[slot],
+                            p->with_n ? p->d_nt[slot] : nullptr, s, p->d_nflag + slot);
+        a.reads = reinterpret_cast<const uint2 *>(p->d_pr[slot]);
+        a.refs = reinterpret_cast<const uint2 *>(p->d_pt[slot]);
+        a.reads_n = p->with_n ? p->d_nr[slot] : nullptr;
+        a.refs_n = p->with_n ? p->d_nt[slot] : nullptr;
+        return e;
+    };
+    return run_chunks(p, n_pairs, E, accept, count, idx, n_accepted, !p->with_n, stage);
+}
+
+shouji_status shouji_pipeline_run_packed(shouji_pipeline *p, const uint32_t *reads,
+                                         const uint32_t *refs, const uint32_t *reads_n,
+                                         const uint32_t *refs_n, size_t n_pairs, int E,
+                                         uint32_t *accept, uint8_t *count, uint32_t *idx,
+                                         uint64_t *n_accepted)
+{
+    if (!p || E < 0 || E > SHOUJI_MAX_E || (!reads_n) != (!refs_n) || (reads_n && !p->with_n))
+        return SHOUJI_EINVAL;
+    if (n_pairs && (!reads || !refs || !accept))
+        return SHOUJI_EINVAL;
+    const uint32_t m = p->m;
+    const bool masks = reads_n != nullptr;
+    auto stage = [&](int slot, size_t base, size_t nc, cudaStream_t s, FilterArgs &a) {
+        // a chunk starts on a tile (the chunk size is a multiple of 1024), so
+        // its packed words and masks are contiguous in the caller's arrays
+        const size_t w0 = shouji_packed_words(base, m), wn = shouji_packed_words(nc, m);
+        cudaError_t e = cudaMemcpyAsync(p->d_pr[slot], reads + w0, wn * 4,
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_pt[slot], refs + w0, wn * 4, cudaMemcpyHostToDevice, s);
+        if (masks) {
+            const size_t n0 = shouji_nmask_words(base, m), nn = shouji_nmask_words(nc, m);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(p->d_nr[slot], reads_n + n0, nn * 4,
+                                    cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(p->d_nt[slot], refs_n + n0, nn * 4,
+                                    cudaMemcpyHostToDevice, s);
+        }
+        a.reads = reinterpret_cast<const uint2 *>(p->d_pr[slot]);
+        a.refs = reinterpret_cast<const uint2 *>(p->d_pt[slot]);
+        a.reads_n = masks ? p->d_nr[slot] : nullptr;
+        a.refs_n = masks ? p->d_nt[slot] : nullptr;
+        return e;
+    };
+    return run_chunks(p, n_pairs, E, accept, count, idx, n_accepted, false, stage);
 }
 
 }  // extern "C"

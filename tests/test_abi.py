@@ -95,6 +95,10 @@ def test_host_argument_checks_return_einval():
               None) == EINVAL
     assert pf(None, None, u64(100), sz(0), 100, 5, None, None, None, None, None) == OK
     assert lib.shouji_selftest_pack_wait(None) == EINVAL
+    # host pipelines: no pipeline
+    assert lib.shouji_pipeline_run(None, fake, fake, 100, 10, 5, fake, None, None, None) == EINVAL
+    assert lib.shouji_pipeline_run_packed(None, fake, fake, None, None, 10, 5, fake, None, None,
+                                          None) == EINVAL
     # compact: short or misaligned workspace, too many pairs, nulls
     assert lib.shouji_compact(fake, 1000, fake, fake, fake, 0, None) == EINVAL
     assert lib.shouji_compact(fake, 1000, fake, fake, ctypes.c_void_p(0x1008), 1 << 20, None) == EINVAL
