@@ -288,6 +288,45 @@ shouji_status shouji_pack_filter_fused(const uint8_t *reads, const uint8_t *refs
                                        uint64_t stride, uint32_t m, int E, int *fused);
 
 /*
+ * shouji_pack_filter_results -- shouji_pack_filter for a caller that wants
+ * only the results (accept bits and counts), not the packed sequences: the
+ * filter of Sec. 2.2 on ASCII pairs, with the same results.
+ *
+ * Where the fused kernel applies (shouji_pack_filter_fused gives 1), each
+ * CTA packs its tiles into a ring of its own in the workspace: the tile of
+ * hand-over slot q goes to ring entry q, over the tile that used the slot
+ * before (the producers wait until it has been filtered).  The rings of all
+ * CTAs take about 93 MB at m = 100, which stays in L2, so the packed words
+ * need not reach HBM.  Otherwise the workspace holds both packed arrays and
+ * the call is shouji_pack_filter.
+ *
+ *   reads, refs, stride, n_pairs, m, E   as shouji_pack_filter.
+ *   workspace   device, 16-byte aligned, at least the bytes that
+ *               shouji_pack_filter_workspace_size gives for the same
+ *               arguments on the current device; its contents are scratch.
+ *   out_accept, out_count                as shouji_pack_filter.
+ * Errors: SHOUJI_EINVAL for NULL pointers (with n_pairs > 0), a short or
+ * misaligned workspace, m, stride or E out of range; SHOUJI_ECUDA on a
+ * launch failure.  Bounded waits as shouji_pack_filter.
+ *
+ * shouji_pack_filter_workspace_size writes that size to *bytes (0 for
+ * n_pairs = 0): 2 * 12 tiles * 256 m bytes per CTA of the fused kernel
+ * (one per SM, at most one per 1024-pair tile), else
+ * 2 * 4 * shouji_packed_words(n_pairs, m).  Errors: SHOUJI_EINVAL for NULL
+ * bytes or m, stride or E out of range; SHOUJI_ECUDA when the device cannot
+ * be queried.
+ */
+shouji_status shouji_pack_filter_workspace_size(const uint8_t *reads, const uint8_t *refs,
+                                                uint64_t stride, size_t n_pairs, uint32_t m,
+                                                int E, size_t *bytes);
+
+shouji_status shouji_pack_filter_results(const uint8_t *reads, const uint8_t *refs,
+                                         uint64_t stride, size_t n_pairs, uint32_t m, int E,
+                                         void *workspace, size_t workspace_bytes,
+                                         uint32_t *out_accept, uint8_t *out_count,
+                                         void *stream);
+
+/*
  * shouji_count -- local and semi-global ("glocal") counting.
  *
  * The paper counts every one of the Shouji bit-vector for end-to-end

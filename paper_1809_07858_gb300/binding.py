@@ -24,7 +24,8 @@ __all__ = [
     "load_library", "shouji_status_string", "shouji_last_cuda_error", "shouji_wait_failures",
     "shouji_selftest_pack_wait", "shouji_alu_probe", "PROBE_OPS", "shouji_unmasked_n",
     "shouji_packed_words", "shouji_nmask_words", "shouji_pack", "shouji_filter",
-    "shouji_pack_filter", "shouji_pack_filter_fused",
+    "shouji_pack_filter", "shouji_pack_filter_fused", "shouji_pack_filter_results",
+    "shouji_pack_filter_workspace_size",
     "shouji_compact_workspace_size", "shouji_compact", "filter_pairs",
     "accept_to_bool", "Pipeline", "shouji_compact_noalloc", "SHOUJI_NOALLOC_MAX_PAIRS",
     "Batch", "Server", "shouji_count", "COUNT_GLOBAL", "COUNT_LOCAL", "COUNT_GLOCAL_START",
@@ -81,6 +82,12 @@ def load_library(path: str = LIB_PATH):
     lib.shouji_pack_filter_fused.argtypes = [vp, vp, u64, u32, ctypes.c_int,
                                              ctypes.POINTER(ctypes.c_int)]
     lib.shouji_pack_filter_fused.restype = ctypes.c_int
+    lib.shouji_pack_filter_workspace_size.argtypes = [vp, vp, u64, sz, u32, ctypes.c_int,
+                                                      ctypes.POINTER(sz)]
+    lib.shouji_pack_filter_workspace_size.restype = ctypes.c_int
+    lib.shouji_pack_filter_results.argtypes = [vp, vp, u64, sz, u32, ctypes.c_int, vp, sz, vp,
+                                               vp, vp]
+    lib.shouji_pack_filter_results.restype = ctypes.c_int
     lib.shouji_compact_workspace_size.argtypes = [sz]
     lib.shouji_compact_workspace_size.restype = sz
     lib.shouji_compact.argtypes = [vp, sz, vp, vp, vp, sz, vp]
@@ -302,6 +309,44 @@ def shouji_pack_filter(reads, refs, m: int, E: int, *, n: int | None = None,
                                   _stream(stream)),
            "shouji_pack_filter")
     return packed_reads, packed_refs, out_accept, out_count
+
+
+def shouji_pack_filter_workspace_size(reads, refs, m: int, E: int, n: int, *,
+                                      stride: int | None = None) -> int:
+    """Bytes of the workspace ``shouji_pack_filter_results`` needs."""
+    stride = (reads.shape[1] if reads.dim() == 2 else m) if stride is None else stride
+    b = ctypes.c_size_t(0)
+    _check(load_library().shouji_pack_filter_workspace_size(_ptr(reads), _ptr(refs), stride, n, m,
+                                                            E, ctypes.byref(b)),
+           "shouji_pack_filter_workspace_size")
+    return b.value
+
+
+def shouji_pack_filter_results(reads, refs, m: int, E: int, *, n: int | None = None,
+                               stride: int | None = None, workspace=None, out_accept=None,
+                               out_count=None, count: bool = True, stream=None):
+    """``shouji_pack_filter`` without the packed outputs (the packed tiles go
+    through per-CTA rings in ``workspace``, a CUDA uint8 tensor of at least
+    ``shouji_pack_filter_workspace_size`` bytes).  Returns ``(accept_words,
+    count)``."""
+    torch = _torch()
+    if reads.dim() == 2:
+        n = reads.shape[0] if n is None else n
+        stride = reads.shape[1] if stride is None else stride
+    assert n is not None and stride is not None
+    dev = reads.device
+    if workspace is None:
+        need = shouji_pack_filter_workspace_size(reads, refs, m, E, n, stride=stride)
+        workspace = torch.empty(max(16, need), dtype=torch.uint8, device=dev)
+    if out_accept is None:
+        out_accept = torch.empty(max(1, (n + 31) // 32), dtype=torch.int32, device=dev)
+    if out_count is None and count:
+        out_count = torch.empty(max(1, n), dtype=torch.uint8, device=dev)
+    _check(load_library().shouji_pack_filter_results(
+        _ptr(reads), _ptr(refs), stride, n, m, E, _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _ptr(out_accept), _ptr(out_count),
+        _stream(stream)), "shouji_pack_filter_results")
+    return out_accept, out_count
 
 
 def shouji_pack_filter_fused(reads, refs, m: int, E: int, *, stride: int | None = None) -> bool:

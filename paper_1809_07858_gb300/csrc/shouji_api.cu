@@ -190,6 +190,82 @@ shouji_status shouji_pack_filter(const uint8_t *reads, const uint8_t *refs, uint
     return cuda_status(launch_filter(a, E, s));
 }
 
+namespace {
+
+// Whether shouji_pack_filter_results runs the fused kernel for these
+// arguments, and the workspace bytes it needs: the per-CTA rings of both
+// sides if so, else both full packed arrays for the separate launches.
+cudaError_t results_plan(const uint8_t *reads, const uint8_t *refs, uint64_t stride,
+                         size_t n_pairs, uint32_t m, int E, bool *fused, size_t *bytes)
+{
+    *fused = false;
+    *bytes = 0;
+    if (n_pairs == 0)
+        return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (stride == m && reads && refs && (uintptr_t)reads % 16 == 0 && (uintptr_t)refs % 16 == 0)
+        e = pack_filter_kernel_applies((int)m, E, fused);
+    if (e != cudaSuccess)
+        return e;
+    if (*fused) {
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        *bytes = 2 * pack_filter_ring_words(n_pairs, (int)m, sms) * 4;
+    } else {
+        *bytes = 2 * shouji_packed_words(n_pairs, m) * 4;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+shouji_status shouji_pack_filter_workspace_size(const uint8_t *reads, const uint8_t *refs,
+                                                uint64_t stride, size_t n_pairs, uint32_t m,
+                                                int E, size_t *bytes)
+{
+    if (!bytes)
+        return SHOUJI_EINVAL;
+    *bytes = 0;
+    if (m < 1 || m > SHOUJI_MAX_M || stride < m || E < 0 || E > SHOUJI_MAX_E)
+        return SHOUJI_EINVAL;
+    bool fused = false;
+    return cuda_status(results_plan(reads, refs, stride, n_pairs, m, E, &fused, bytes));
+}
+
+shouji_status shouji_pack_filter_results(const uint8_t *reads, const uint8_t *refs,
+                                         uint64_t stride, size_t n_pairs, uint32_t m, int E,
+                                         void *workspace, size_t workspace_bytes,
+                                         uint32_t *out_accept, uint8_t *out_count, void *stream)
+{
+    if (m < 1 || m > SHOUJI_MAX_M || stride < m || E < 0 || E > SHOUJI_MAX_E)
+        return SHOUJI_EINVAL;
+    if (n_pairs == 0)
+        return SHOUJI_OK;
+    if (!reads || !refs || !workspace || !out_accept || (uintptr_t)workspace % 16)
+        return SHOUJI_EINVAL;
+    bool fused = false;
+    size_t need = 0;
+    const cudaError_t e = results_plan(reads, refs, stride, n_pairs, m, E, &fused, &need);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (workspace_bytes < need)
+        return SHOUJI_EINVAL;
+    uint32_t *side_r = static_cast<uint32_t *>(workspace);
+    uint32_t *side_t = side_r + need / 8;   // the two halves of the workspace
+    if (fused) {
+        const cudaError_t f = launch_pack_filter(reads, refs, n_pairs, (int)m, E, side_r, side_t,
+                                                 out_accept, out_count, (cudaStream_t)stream,
+                                                 true);
+        if (f != cudaErrorNotSupported)
+            return cuda_status(f);
+        return SHOUJI_ECUDA;  // the kernel applied a moment ago
+    }
+    return shouji_pack_filter(reads, refs, stride, n_pairs, m, E, side_r, side_t, out_accept,
+                              out_count, stream);
+}
+
 shouji_status shouji_pack_filter_fused(const uint8_t *reads, const uint8_t *refs,
                                        uint64_t stride, uint32_t m, int E, int *fused)
 {

@@ -39,10 +39,16 @@ bool pack_filter_fusable(int m, int E);
 // m) on 16-byte boundaries, no N masks or per-pair thresholds (checked by
 // the caller).  cudaErrorNotSupported, with nothing launched, when the
 // kernel does not apply (pack_filter_fusable, or a compiled register count
-// other than the one its register split assumes).
+// other than the one its register split assumes).  ring_mode: packed_r and
+// packed_t are per-CTA rings of pack_filter_ring_words() words each instead
+// of packed outputs.
 cudaError_t launch_pack_filter(const uint8_t *reads, const uint8_t *refs, size_t n, int m, int E,
                                uint32_t *packed_r, uint32_t *packed_t, uint32_t *accept,
-                               uint8_t *count, cudaStream_t s);
+                               uint8_t *count, cudaStream_t s, bool ring_mode = false);
+// CTAs of the fused kernel for n pairs on a GPU of `sms` SMs, and the words of
+// one side's rings in ring mode (a queue slot's tile per CTA and slot).
+size_t pack_filter_grid(size_t n, int sms);
+size_t pack_filter_ring_words(size_t n, int m, int sms);
 // Whether launch_pack_filter would run the fused kernel for length m and
 // threshold E (pack_filter_fusable and the compiled register count).
 cudaError_t pack_filter_kernel_applies(int m, int E, bool *applies);

@@ -103,7 +103,9 @@ struct FusedArgs {
     const uint8_t *reads, *refs;   // n rows of m ASCII bytes each, contiguous
     size_t n;
     int m;
-    uint32_t *packed_r, *packed_t; // packed outputs (layout of shouji_pack)
+    uint32_t *packed_r, *packed_t; // packed outputs (layout of shouji_pack), or the rings
+    int ring_mode;                 // 1: tile t goes to entry blockIdx.x * kSlots + t % kSlots
+                                   // of packed_r / packed_t (per-CTA rings, no output)
     uint32_t *accept;
     uint8_t *count;
     int rot_step;
@@ -179,27 +181,34 @@ __device__ void produce(const FusedArgs &a, uint8_t *ring, uint64_t *full, uint6
             break;
         }
         const size_t t = T0 + i / kBlocksPerTile;
-        uint32_t *dst = (i / kHalfBlocks) % 2 ? a.packed_t : a.packed_r;
-        const int lane0 = (int)(i % kHalfBlocks) * kBlockLanes;
-        if constexpr (LAYOUT == 2)
-            seen |= pack_transpose_w_odd(reinterpret_cast<const uint32_t *>(buf), a.m, t, lane0,
-                                         dst, kGroupThreads, gtid);
-        else
-            seen |= pack_transpose_by<false, LAYOUT == 1, kBlockLanes>(
-                reinterpret_cast<const uint32_t *>(buf), a.m, a.m, t, lane0, dst, nullptr,
-                a.rot_step, kGroupThreads, gtid);
-        if (i % kBlocksPerTile >= kBlocksPerTile - kGroups) {  // the group's last block of t
-            const int slot = (int)((t - T0) % kSlots);
-            const size_t k = (t - T0) / kSlots;
-            const bool was_freed =
-                k == 0 || mbar_wait_bounded(&freed[slot], (uint32_t)((k - 1) & 1));
+        const int slot = (int)((t - T0) % kSlots);
+        const size_t k = (t - T0) / kSlots;
+        // The producers complete tile t only after tile t - kSlots is freed.
+        // In ring mode tile t is written over the ring entry of tile t - kSlots,
+        // so the wait comes before the group's first block of t instead of
+        // before its last.
+        const bool first = i % kBlocksPerTile < kGroups;
+        const bool last = i % kBlocksPerTile >= kBlocksPerTile - kGroups;
+        if (k > 0 && (a.ring_mode ? first : last)) {
+            const bool was_freed = mbar_wait_bounded(&freed[slot], (uint32_t)((k - 1) & 1));
             if (group_sync_or(g, !was_freed)) {
                 failed = true;
                 ++j;
                 break;
             }
-            mbar_arrive(&ready[slot]);  // release: this thread's words of tile t
         }
+        const size_t wt = a.ring_mode ? (size_t)blockIdx.x * kSlots + slot : t;
+        uint32_t *dst = (i / kHalfBlocks) % 2 ? a.packed_t : a.packed_r;
+        const int lane0 = (int)(i % kHalfBlocks) * kBlockLanes;
+        if constexpr (LAYOUT == 2)
+            seen |= pack_transpose_w_odd(reinterpret_cast<const uint32_t *>(buf), a.m, wt, lane0,
+                                         dst, kGroupThreads, gtid);
+        else
+            seen |= pack_transpose_by<false, LAYOUT == 1, kBlockLanes>(
+                reinterpret_cast<const uint32_t *>(buf), a.m, a.m, wt, lane0, dst, nullptr,
+                a.rot_step, kGroupThreads, gtid);
+        if (last)
+            mbar_arrive(&ready[slot]);  // release: this thread's words of tile t
         group_sync(g);  // buffer b may be refilled
     }
     if (failed) {
@@ -244,7 +253,8 @@ __device__ void consume(const FusedArgs &a, uint64_t *ready, uint64_t *freed,
             mbar_arrive(&freed[slot]);
             continue;
         }
-        const size_t base = t * (size_t)m * kLanes + lane;
+        const size_t wt = a.ring_mode ? (size_t)blockIdx.x * kSlots + slot : t;
+        const size_t base = wt * (size_t)m * kLanes + lane;
         filt::View v;
         v.rd = reinterpret_cast<const uint2 *>(a.packed_r) + base;
         v.rf = reinterpret_cast<const uint2 *>(a.packed_t) + base;
@@ -356,8 +366,7 @@ cudaError_t launch_fused_ta(const FusedArgs &a, cudaStream_t s)
         return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    const size_t n_tiles = tiles_of(a.n);
-    const unsigned grid = (unsigned)(n_tiles < (size_t)sms ? n_tiles : (size_t)sms);
+    const unsigned grid = (unsigned)pack_filter_grid(a.n, sms);
     pack_filter_kernel<E, LAYOUT><<<grid, kFusedThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -412,9 +421,20 @@ cudaError_t pack_filter_kernel_applies(int m, int E, bool *applies)
     return e;
 }
 
+size_t pack_filter_grid(size_t n, int sms)
+{
+    const size_t n_tiles = tiles_of(n);
+    return n_tiles < (size_t)sms ? n_tiles : (size_t)sms;
+}
+
+size_t pack_filter_ring_words(size_t n, int m, int sms)
+{
+    return pack_filter_grid(n, sms) * kSlots * (size_t)m * kLanes * 2;
+}
+
 cudaError_t launch_pack_filter(const uint8_t *reads, const uint8_t *refs, size_t n, int m, int E,
                                uint32_t *packed_r, uint32_t *packed_t, uint32_t *accept,
-                               uint8_t *count, cudaStream_t s)
+                               uint8_t *count, cudaStream_t s, bool ring_mode)
 {
     if (!pack_filter_fusable(m, E))
         return cudaErrorNotSupported;
@@ -425,6 +445,7 @@ cudaError_t launch_pack_filter(const uint8_t *reads, const uint8_t *refs, size_t
     a.m = m;
     a.packed_r = packed_r;
     a.packed_t = packed_t;
+    a.ring_mode = ring_mode ? 1 : 0;
     a.accept = accept;
     a.count = count;
     a.rot_step = rotation_step(m, kBlockLanes);

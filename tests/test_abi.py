@@ -94,6 +94,27 @@ def test_host_argument_checks_return_einval():
     assert pf(fake, fake, u64(100), sz(10), 100, 5, ctypes.c_void_p(0x1004), fake, fake, None,
               None) == EINVAL
     assert pf(None, None, u64(100), sz(0), 100, 5, None, None, None, None, None) == OK
+    # pack_filter_results / its workspace size: nulls, short or misaligned
+    # workspace, m, stride or E out of range (none of these needs a device)
+    pr = lib.shouji_pack_filter_results
+    assert pr(fake, fake, u64(100), sz(10), 0, 5, fake, sz(1 << 20), fake, None, None) == EINVAL
+    assert pr(fake, fake, u64(99), sz(10), 100, 5, fake, sz(1 << 20), fake, None, None) == EINVAL
+    assert pr(fake, fake, u64(100), sz(10), 100, 32, fake, sz(1 << 20), fake, None, None) == EINVAL
+    assert pr(None, fake, u64(100), sz(10), 100, 5, fake, sz(1 << 20), fake, None, None) == EINVAL
+    assert pr(fake, fake, u64(100), sz(10), 100, 5, None, sz(1 << 20), fake, None, None) == EINVAL
+    assert pr(fake, fake, u64(100), sz(10), 100, 5, fake, sz(1 << 20), None, None, None) == EINVAL
+    assert pr(fake, fake, u64(100), sz(10), 100, 5, ctypes.c_void_p(0x1008), sz(1 << 20), fake,
+              None, None) == EINVAL
+    assert pr(None, None, u64(100), sz(0), 100, 5, None, sz(0), None, None, None) == OK
+    ws = lib.shouji_pack_filter_workspace_size
+    b = sz(7)
+    assert ws(fake, fake, u64(100), sz(10), 100, 5, None) == EINVAL
+    assert ws(fake, fake, u64(100), sz(10), 256, 5, ctypes.byref(b)) == EINVAL and b.value == 0
+    assert ws(fake, fake, u64(100), sz(10), 100, -1, ctypes.byref(b)) == EINVAL
+    assert ws(fake, fake, u64(100), sz(0), 100, 5, ctypes.byref(b)) == OK and b.value == 0
+    # rows that are not contiguous never take the fused kernel: both packed arrays
+    assert ws(fake, fake, u64(112), sz(5000), 100, 5, ctypes.byref(b)) == OK
+    assert b.value == 2 * 4 * sj.shouji_packed_words(5000, 100)
     assert lib.shouji_selftest_pack_wait(None) == EINVAL
     # host pipelines: no pipeline
     assert lib.shouji_pipeline_run(None, fake, fake, 100, 10, 5, fake, None, None, None) == EINVAL

@@ -16,6 +16,12 @@ it took, with all its producer arrivals and no arrival of another tile in the
 same phase, and that the actors never deadlock.  Two planted mistakes must
 fail the check: producers that skip the `freed` wait, and a queue with fewer
 slots than filter warps.
+
+Ring mode (shouji_pack_filter_results): tile t is packed into the ring entry
+of slot s, over tile t - S, so each group waits for `freed[s]` phase k - 1
+before its first block of t (not before its last), and no block of t may be
+written while a filter warp still reads the entry.  With the wait before the
+last block instead (a planted mistake) that check fails.
 """
 import os
 import random
@@ -50,9 +56,12 @@ class Barrier:
 
 
 class Producer:
-    def __init__(self, g, n_tiles, ready, freed, slots, wait_freed=True):
+    def __init__(self, g, n_tiles, ready, freed, slots, wait_freed=True, ring=None,
+                 wait_at_first=False):
         self.g, self.ready, self.freed, self.wait_freed = g, ready, freed, wait_freed
         self.slots = slots
+        self.ring = ring                  # ring mode: slot -> tile being read, or None
+        self.wait_at_first = wait_at_first
         self.blocks = list(range(g, n_tiles * BLOCKS, GROUPS))
         self.pos = 0
 
@@ -63,11 +72,17 @@ class Producer:
         """Packs one block; at the group's last block of a tile, hands the tile
         over.  False when blocked on `freed`."""
         i = self.blocks[self.pos]
-        if i % BLOCKS >= BLOCKS - GROUPS:
-            t = i // BLOCKS
-            s, k = t % self.slots, t // self.slots
-            if self.wait_freed and k > 0 and not self.freed[s].try_wait((k - 1) & 1):
+        t = i // BLOCKS
+        s, k = t % self.slots, t // self.slots
+        first, last = i % BLOCKS < GROUPS, i % BLOCKS >= BLOCKS - GROUPS
+        if self.wait_freed and k > 0 and (first if self.wait_at_first else last):
+            if not self.freed[s].try_wait((k - 1) & 1):
                 return False
+        if self.ring is not None:
+            # the block's words go to the ring entry of slot s
+            assert self.ring[s] is None, "tile %d written over tile %d, still being read" % (
+                t, self.ring[s])
+        if last:
             self.ready[s].arrive(t)
         self.pos += 1
         return True
@@ -79,9 +94,10 @@ class Queue:
 
 
 class Consumer:
-    def __init__(self, w, queue, ready, freed, slots, rng):
+    def __init__(self, w, queue, ready, freed, slots, rng, ring=None):
         self.w, self.q, self.ready, self.freed, self.rng = w, queue, ready, freed, rng
         self.slots = slots
+        self.ring = ring
         self.tile = None   # the tile taken, not yet accepted
         self.work = 0      # filter steps left on the accepted tile
         self.finished = False
@@ -113,20 +129,29 @@ class Consumer:
             self.work = 1 + self.rng.randrange(12)
             self.tile = None
             self.accepted = r
+            if self.ring is not None:
+                self.ring[s] = r          # reads the entry until it frees the slot
             return True
         self.work -= 1
         if self.work == 0:
+            if self.ring is not None:
+                self.ring[self.accepted % self.slots] = None
             self.freed[self.accepted % self.slots].arrive(self.accepted)
         return True
 
 
-def run(n_tiles, seed, wait_freed=True, slots=SLOTS, producer_turns=6):
+def run(n_tiles, seed, wait_freed=True, slots=SLOTS, producer_turns=6, ring_mode=False,
+        wait_at_first=None):
     rng = random.Random(seed)
     ready = [Barrier(GROUPS) for _ in range(slots)]
     freed = [Barrier(1) for _ in range(slots)]
     queue = Queue(n_tiles)
-    actors = [Producer(g, n_tiles, ready, freed, slots, wait_freed) for g in range(GROUPS)]
-    consumers = [Consumer(w, queue, ready, freed, slots, rng) for w in range(CONSUMERS)]
+    ring = [None] * slots if ring_mode else None
+    if wait_at_first is None:
+        wait_at_first = ring_mode
+    actors = [Producer(g, n_tiles, ready, freed, slots, wait_freed, ring, wait_at_first)
+              for g in range(GROUPS)]
+    consumers = [Consumer(w, queue, ready, freed, slots, rng, ring) for w in range(CONSUMERS)]
     actors += consumers
     while True:
         live = [a for a in actors if not a.done()]
@@ -179,6 +204,25 @@ def test_handover_with_fewer_slots_than_filter_warps_fails():
     for seed in range(40):
         try:
             run(64, seed, slots=4)
+        except AssertionError:
+            failures += 1
+    assert failures > 0
+
+
+@pytest.mark.parametrize("n_tiles", [1, 2, 7, 11, 12, 13, 24, 25, 64, 193])
+def test_ring_mode_never_overwrites_a_tile_being_read(n_tiles):
+    for seed in range(40):
+        run(n_tiles, seed, ring_mode=True, producer_turns=50)
+
+
+def test_ring_mode_with_the_wait_before_the_last_block_fails():
+    """Planted mistake: in ring mode, waiting for `freed` only before the
+    last block of a tile lets the first blocks overwrite a tile still being
+    filtered."""
+    failures = 0
+    for seed in range(40):
+        try:
+            run(64, seed, ring_mode=True, wait_at_first=False, producer_turns=200)
         except AssertionError:
             failures += 1
     assert failures > 0

@@ -179,3 +179,57 @@ def test_without_counts_on_a_side_stream_with_reused_outputs():
         assert (accept_bits(acc, n) == acc_o).all()
         assert (unpack_planes(pr.cpu().numpy(), n, m) == CODE[reads]).all()
         assert (unpack_planes(pt.cpu().numpy(), n, m) == CODE[refs]).all()
+
+
+# ---------------------------------------------------------------- results only
+def check_results(reads, refs, m, E):
+    """shouji_pack_filter_results: the packed tiles go through per-CTA rings in
+    a workspace that starts out as garbage; accept bits and counts against
+    the oracle."""
+    d = dev()
+    n = len(reads)
+    r = torch.from_numpy(np.ascontiguousarray(reads)).to(d)
+    t = torch.from_numpy(np.ascontiguousarray(refs)).to(d)
+    need = sj.shouji_pack_filter_workspace_size(r, t, m, E, n)
+    if sj.shouji_pack_filter_fused(r, t, m, E):
+        # 12 tiles of 256 m bytes per CTA (one per SM, at most one per tile) and side
+        sms = torch.cuda.get_device_properties(d).multi_processor_count
+        assert need == 2 * min((n + 1023) // 1024, sms) * 12 * 256 * m
+    else:
+        assert need == 2 * 4 * sj.shouji_packed_words(n, m)
+    ws = torch.full((need,), 0xAB, dtype=torch.uint8, device=d)
+    acc, cnt = sj.shouji_pack_filter_results(r, t, m, E, workspace=ws)
+    torch.cuda.synchronize()
+    assert sj.shouji_wait_failures() == 0
+    acc_o, cnt_o = oracle.shouji_batch(reads, refs, E, threads=8)
+    got_cnt = cnt[:n].cpu().numpy()
+    bad = np.flatnonzero((got_cnt != cnt_o) | (accept_bits(acc, n) != acc_o))
+    assert bad.size == 0, "%d pairs differ, first %s" % (bad.size, bad[:10])
+    words = acc.cpu().numpy().view(np.uint32)
+    if n % 32:
+        assert words[-1] >> (n % 32) == 0, "accept bits past n"
+
+
+@pytest.mark.parametrize("n,m,E", [
+    (1, 100, 5), (1025, 100, 5), (155_649, 100, 5),
+    (2_500_003, 100, 5),      # about 16 tiles per CTA: every ring entry is reused
+    (300_001, 64, 3), (200_000, 37, 5), (100_000, 199, 4), (120_000, 100, 0),
+    (50_000, 100, 7),         # above the fused thresholds: the separate launches
+])
+def test_results_without_packed_outputs(n, m, E):
+    reads, refs = pairs(n, m, E, 900 + n % 1000 + m)
+    check_results(reads, refs, m, E)
+
+
+def test_results_workspace_checks():
+    d = dev()
+    reads, refs = pairs(5000, 100, 5, 5)
+    r = torch.from_numpy(reads).to(d)
+    t = torch.from_numpy(refs).to(d)
+    need = sj.shouji_pack_filter_workspace_size(r, t, 100, 5, 5000)
+    ws = torch.empty(need + 64, dtype=torch.uint8, device=d)
+    with pytest.raises(sj.ShoujiError):          # one byte short
+        sj.shouji_pack_filter_results(r, t, 100, 5, workspace=ws[:need - 1])
+    with pytest.raises(sj.ShoujiError):          # off the 16-byte boundary
+        sj.shouji_pack_filter_results(r, t, 100, 5, workspace=ws[8:need + 8])
+    assert sj.shouji_pack_filter_workspace_size(r, t, 100, 5, 0) == 0

@@ -4,8 +4,10 @@
 with 'N' bases: every pair is filtered on the GPU and recomputed by the oracle
 (one pair at a time, on all host cores), and the two must match bit for bit on
 every pair; properties that hold for every pair are checked as well.  Without
-N masks the fused pack + filter (shouji_pack_filter, the benchmark's step) is
-checked the same way, and its packed words against shouji_pack's.
+N masks the fused pack + filter (shouji_pack_filter) is checked the same way,
+and its packed words against shouji_pack's, and so is the benchmark's step
+(shouji_pack_filter_results: the same kernel with the packed tiles in per-CTA
+rings instead of packed outputs).
 """
 import os
 import numpy as np
@@ -30,13 +32,18 @@ def run_full(reads, refs, m, E, with_n):
     t = torch.from_numpy(refs).to(dev)
     pr, nr = sj.shouji_pack(r, m, with_n=with_n)
     pt, nt = sj.shouji_pack(t, m, with_n=with_n)
-    fused = None
+    fused = results = None
     if not with_n:
         fr, ft, facc, fcnt = sj.shouji_pack_filter(r, t, m, E)
         torch.cuda.synchronize()
         same_packing = bool(torch.equal(fr, pr)) and bool(torch.equal(ft, pt))
         fused = (sj.accept_to_bool(facc, n).cpu().numpy(), fcnt[:n].cpu().numpy(), same_packing)
         del fr, ft, facc, fcnt
+        # the same without packed outputs (per-CTA rings in a workspace)
+        racc, rcnt = sj.shouji_pack_filter_results(r, t, m, E)
+        torch.cuda.synchronize()
+        results = (sj.accept_to_bool(racc, n).cpu().numpy(), rcnt[:n].cpu().numpy())
+        del racc, rcnt
     del r, t
     acc, cnt, _ = sj.shouji_filter(pr, pt, m, n, E, reads_nmask=nr, refs_nmask=nt)
     idx, n_acc = sj.shouji_compact(acc, n)
@@ -46,14 +53,14 @@ def run_full(reads, refs, m, E, with_n):
     k = int(n_acc.item())
     survivors = idx[:k].cpu().numpy()
     assert sj.shouji_wait_failures() == 0
-    return accept, count, survivors, fused
+    return accept, count, survivors, fused, results
 
 
 def check(reads, refs, m, E, with_n):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     n = len(reads)
-    accept, count, survivors, fused = run_full(reads, refs, m, E, with_n)
+    accept, count, survivors, fused, results = run_full(reads, refs, m, E, with_n)
     # properties over every pair
     assert (count <= m).all()
     assert (accept == (count <= E)).all()
@@ -69,6 +76,10 @@ def check(reads, refs, m, E, with_n):
         assert same_packing, "fused pack + filter wrote other packed words"
         bad = np.flatnonzero((f_cnt != cnt_o) | (f_acc != acc_o))
         assert bad.size == 0, "fused: %d pairs differ, first %s" % (bad.size, bad[:10])
+    if results is not None:
+        r_acc, r_cnt = results
+        bad = np.flatnonzero((r_cnt != cnt_o) | (r_acc != acc_o))
+        assert bad.size == 0, "results only: %d pairs differ, first %s" % (bad.size, bad[:10])
 
 
 @pytest.mark.parametrize("E", [0, 5, 10])
