@@ -520,7 +520,9 @@ def run_served(args, dev):
     (summed GPU time of the requests over the time any was on the GPU).  The
     same at capacity with the reference segments resident on the device
     (requests send reads and offsets only)."""
+    import queue as queue_mod
     import threading
+    from concurrent.futures import ThreadPoolExecutor
 
     import numpy as np
     import torch
@@ -545,8 +547,8 @@ def run_served(args, dev):
     ref_id = srv.add_reference(h_refs.view(-1))
     rng = np.random.default_rng(99)
 
-    def submit(i, size, off, resident):
-        a, c = outs[i % ring]
+    def submit(b, size, off, resident):
+        a, c = outs[b]
         if resident:
             return srv.submit_at(h_reads[off:off + size], ref_id, h_off[off:off + size],
                                  h_lens[off:off + size], h_E[off:off + size], a, c,
@@ -556,14 +558,27 @@ def run_served(args, dev):
 
     def drive(n_req, rate=None, inflight=None, resident=False):
         """rate: Poisson arrivals per second; inflight: closed loop with that
-        many requests outstanding."""
+        many requests outstanding.  Requests are waited for in any order (a
+        pool of waiter threads), so that one long request does not hold back
+        the admission of the next ones; output buffers come from a free list."""
         sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=n_req)).astype(np.int64)
         offs = rng.integers(0, pool - sizes + 1)
         gaps = rng.exponential(1.0 / rate, size=n_req) if rate else None
-        ids = [None] * n_req
-        ready = [threading.Event() for _ in range(n_req)]
         res = [None] * n_req
-        free = threading.Semaphore(inflight if inflight else ring)
+        limit = inflight if inflight else ring
+        free = threading.Semaphore(limit)
+        bufs = queue_mod.SimpleQueue()
+        for b in range(ring):
+            bufs.put(b)
+
+        def waiter(i, rid, b):
+            try:
+                res[i] = srv.wait_timed(rid, timeout=120)
+            finally:
+                bufs.put(b)
+                free.release()
+
+        waiters = ThreadPoolExecutor(max_workers=limit)
 
         def submitter():
             t_next = time.perf_counter()
@@ -574,18 +589,17 @@ def run_served(args, dev):
                     if delay > 0:
                         time.sleep(delay)
                 free.acquire()
-                ids[i] = submit(i, int(sizes[i]), int(offs[i]), resident)
-                ready[i].set()
+                b = bufs.get()
+                rid = submit(b, int(sizes[i]), int(offs[i]), resident)
+                waiters.submit(waiter, i, rid, b)
 
         t0 = time.perf_counter()
         th = threading.Thread(target=submitter)
         th.start()
-        for i in range(n_req):
-            ready[i].wait()
-            res[i] = srv.wait_timed(ids[i], timeout=120)
-            free.release()
-        wall = time.perf_counter() - t0
         th.join()
+        waiters.shutdown(wait=True)
+        wall = time.perf_counter() - t0
+        assert all(r is not None for r in res)
         lat_ms = np.array([r[0] for r in res]) * 1e3
         spans = [(r[1], r[2]) for r in res]
         busy = union_length(spans)

@@ -40,7 +40,8 @@ __device__ unsigned int g_batch_unmasked_n;
 
 constexpr int kClsThreads = 256;
 constexpr int kClsItems = 16;                       // pairs per thread
-constexpr int kClsPairs = kClsThreads * kClsItems;  // pairs per CTA
+constexpr int kClsPairs = kClsThreads * kClsItems;  // pairs per chunk
+constexpr int kClsCtasPerSm = 4;                    // 40 KB of shared memory each
 constexpr int kPackThreads = 128;
 constexpr int kPackSeqs = 128;   // 4 lanes of a tile per CTA
 constexpr int kPackLanes = kPackSeqs / 32;
@@ -71,63 +72,85 @@ __device__ __forceinline__ uint32_t lanemask_lt()
 }
 
 // ---------------------------------------------------------------- classify
+// Persistent: each CTA walks chunks of kClsPairs pairs (blockIdx.x, +gridDim.x,
+// ...).  Per chunk, every pair gets its rank among the chunk's pairs of its
+// bucket from a shared histogram (warp-aggregated increments); the first
+// increment of a bucket lists it, and only the listed buckets are reserved
+// in the global histogram (one atomic per bucket and chunk) and cleared for
+// the next chunk.
 __global__ void __launch_bounds__(kClsThreads)
 classify_kernel(const Args *__restrict__ a, int max_m, int e_lo, int e_hi,
                 uint32_t *__restrict__ hist, Tables *__restrict__ T,
                 uint16_t *__restrict__ keys, uint32_t *__restrict__ ranks)
 {
     __shared__ uint32_t sh[kBins];
+    __shared__ uint16_t touched[kClsPairs];   // buckets a chunk's pairs fell in
+    __shared__ uint32_t n_touched;
     const uint64_t n = a->n;
-    const uint64_t i0 = (uint64_t)blockIdx.x * kClsPairs;
-    if (i0 >= n)
+    const uint64_t chunks = (n + kClsPairs - 1) / kClsPairs;
+    if (blockIdx.x >= chunks)
         return;
     for (int k = threadIdx.x; k < kBins; k += kClsThreads)
         sh[k] = 0u;
+    if (threadIdx.x == 0)
+        n_touched = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    uint16_t key[kClsItems];
-    uint32_t local[kClsItems];
     uint32_t bad = 0;
+    for (uint64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+        const uint64_t i0 = c * kClsPairs;
+        uint16_t key[kClsItems];
+        uint32_t local[kClsItems];
 #pragma unroll
-    for (int t = 0; t < kClsItems; ++t) {
-        const uint64_t i = i0 + (uint64_t)t * kClsThreads + threadIdx.x;
-        int k = -1;
-        if (i < n) {
-            const int m = a->lens[i];
-            const int e = a->E_per_pair[i];
-            if (m >= 1 && m <= max_m && e >= e_lo && e <= e_hi)
-                k = m * kMaxE + e;
-            else
-                ++bad;
+        for (int t = 0; t < kClsItems; ++t) {
+            const uint64_t i = i0 + (uint64_t)t * kClsThreads + threadIdx.x;
+            int k = -1;
+            if (i < n) {
+                const int m = a->lens[i];
+                const int e = a->E_per_pair[i];
+                if (m >= 1 && m <= max_m && e >= e_lo && e <= e_hi)
+                    k = m * kMaxE + e;
+                else
+                    ++bad;
+            }
+            // warp-aggregated increment of the shared bucket counter
+            const uint32_t peers = __match_any_sync(0xffffffffu, k);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (lane == leader && k >= 0) {
+                base = atomicAdd(&sh[k], (uint32_t)__popc(peers));
+                if (base == 0)
+                    touched[atomicAdd(&n_touched, 1u)] = (uint16_t)k;
+            }
+            base = __shfl_sync(0xffffffffu, base, leader);
+            key[t] = k >= 0 ? (uint16_t)k : kBadKey;
+            local[t] = base + __popc(peers & lanemask_lt());
         }
-        // warp-aggregated increment of the shared bucket counter
-        const uint32_t peers = __match_any_sync(0xffffffffu, k);
-        const int leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if (lane == leader && k >= 0)
-            base = atomicAdd(&sh[k], (uint32_t)__popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        key[t] = k >= 0 ? (uint16_t)k : kBadKey;
-        local[t] = base + __popc(peers & lanemask_lt());
+        __syncthreads();
+        const uint32_t nt = n_touched;
+        // one global reservation per bucket of this chunk
+        for (uint32_t q = threadIdx.x; q < nt; q += kClsThreads) {
+            const int k = touched[q];
+            sh[k] = atomicAdd(&hist[k], sh[k]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kClsItems; ++t) {
+            const uint64_t i = i0 + (uint64_t)t * kClsThreads + threadIdx.x;
+            if (i < n) {
+                keys[i] = key[t];
+                ranks[i] = key[t] != kBadKey ? sh[key[t]] + local[t] : 0u;
+            }
+        }
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < nt; q += kClsThreads)
+            sh[touched[q]] = 0u;
+        if (threadIdx.x == 0)
+            n_touched = 0u;
+        __syncthreads();
     }
     if (bad)
         atomicAdd(&T->n_invalid, bad);
-    __syncthreads();
-    // one global reservation per non-empty bucket of this CTA
-    for (int k = threadIdx.x; k < kBins; k += kClsThreads) {
-        const uint32_t c = sh[k];
-        if (c)
-            sh[k] = atomicAdd(&hist[k], c);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < kClsItems; ++t) {
-        const uint64_t i = i0 + (uint64_t)t * kClsThreads + threadIdx.x;
-        if (i < n) {
-            keys[i] = key[t];
-            ranks[i] = key[t] != kBadKey ? sh[key[t]] + local[t] : 0u;
-        }
-    }
 }
 
 // ---------------------------------------------------------------- scan
@@ -137,12 +160,16 @@ scan_kernel(const uint32_t *__restrict__ hist, Tables *__restrict__ T)
     __shared__ uint32_t pad_m[kMaxM];   // slots of m-class m (bucket pads to 32, tile pad)
     __shared__ uint32_t mc_of[kMaxM];
     __shared__ uint32_t start_m[kMaxM];
+    __shared__ uint32_t h[kBins];       // the histogram: every pass below reads it here
     const int t = threadIdx.x;
+    for (int k = t; k < kBins; k += 256)
+        h[k] = hist[k];
+    __syncthreads();
     {
         uint32_t p = 0;
         if (t >= 1)
             for (int e = 0; e < kMaxE; ++e)
-                p += (hist[t * kMaxE + e] + 31u) & ~31u;
+                p += (h[t * kMaxE + e] + 31u) & ~31u;
         pad_m[t] = (p + kTile - 1) / kTile * kTile;
     }
     __syncthreads();
@@ -172,7 +199,7 @@ scan_kernel(const uint32_t *__restrict__ hist, Tables *__restrict__ T)
         uint32_t s = start_m[t];
         for (int e = 0; e < kMaxE; ++e) {
             T->bin_slot[t * kMaxE + e] = s;
-            s += (hist[t * kMaxE + e] + 31u) & ~31u;
+            s += (h[t * kMaxE + e] + 31u) & ~31u;
         }
     }
     __syncthreads();
@@ -180,15 +207,15 @@ scan_kernel(const uint32_t *__restrict__ hist, Tables *__restrict__ T)
         const int e = t;
         uint32_t cnt = 0, gs = 0;
         for (int m = 1; m < kMaxM; ++m) {
-            const uint32_t h = hist[m * kMaxE + e];
-            if (h) {
+            const uint32_t c = h[m * kMaxE + e];
+            if (c) {
                 const int b = e * kMaxM + cnt;
                 T->bk_m[b] = m;
                 T->bk_slot[b] = T->bin_slot[m * kMaxE + e];
-                T->bk_count[b] = h;
+                T->bk_count[b] = c;
                 T->bk_gstart[b] = gs;
                 T->bk_mc[b] = mc_of[m];
-                gs += (h + 31u) / 32u;
+                gs += (c + 31u) / 32u;
                 ++cnt;
             }
         }
@@ -642,7 +669,10 @@ cudaError_t enqueue_prologue(shouji_batch *b, cudaStream_t s, int k, bool timed)
         return e;
     if ((e = cudaMemsetAsync(b->d_tables->work, 0, sizeof(uint32_t) * kMaxE, s)))
         return e;
-    const unsigned cls_blocks = (unsigned)((b->max_pairs + kClsPairs - 1) / kClsPairs);
+    // a persistent grid: each CTA walks chunks of kClsPairs pairs
+    const size_t cls_chunks = (b->max_pairs + kClsPairs - 1) / kClsPairs;
+    const size_t cls_cap = (size_t)b->sms * kClsCtasPerSm;
+    const unsigned cls_blocks = (unsigned)(cls_chunks < cls_cap ? cls_chunks : cls_cap);
     classify_kernel<<<cls_blocks ? cls_blocks : 1, kClsThreads, 0, s>>>(
         b->d_args, (int)b->max_m, b->e_lo, b->e_hi, b->d_hist, b->d_tables, b->d_keys, b->d_ranks);
     scan_kernel<<<1, 256, 0, s>>>(b->d_hist, b->d_tables);
