@@ -41,9 +41,9 @@ E = 5
 # from one ncu capture, keyed by the hash of the filter kernel source it was
 # taken on; scaled to a 30M-pair launch.  Reported as null once the kernel
 # source changes.
-FILTER_TRAFFIC = {"1e05717a759a6a6a": 1.537e9}  # profiles/filter_kernel_E5_m100.md
+FILTER_TRAFFIC = {"1e05717a759a6a6a": 1.537e9}  # filter_kernel<5>, m=100, 4M-pair capture
 # The same for the fused pack + filter kernel, keyed by the hash of its sources.
-FUSED_TRAFFIC = {"a9e5bfbf3c497c56": 7.27e9}  # profiles/pack_filter_kernel_m100_E5.md
+FUSED_TRAFFIC = {"a9e5bfbf3c497c56": 7.27e9}  # rings, m=100, E=5, 4M-pair capture
 FUSED_SOURCES = ("shouji_pack_filter.cu", "shouji_pack.cuh", "shouji_filter.cuh")
 
 
