@@ -210,7 +210,8 @@ def workload_config(n):
                         "ASCII resident in HBM; step = pack reads and refs + filter (one fused "
                         "kernel on the GPU) + compact" % n,
             "n_pairs": n, "m": M, "E": E,
-            "l2": "inputs larger than L2 (%.1f GB ASCII per step); no flush" % (2 * n * M / 1e9)}
+            "l2": "inputs larger than L2 (%.1f GB ASCII per step); no flush" % (2 * n * M / 1e9),
+            "step": "results-only fused pack + filter (packed tiles in per-CTA rings) + compact"}
 
 
 def cpu_oracle_rate(reads, refs, threads, magnet=False):
@@ -241,7 +242,11 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic", "config": dict(workload_config(sample), sample=sample_desc),
+        "data": "synthetic",
+        # the same workload as the GPU arm (args.n pairs); each step times a sample of it
+        "config": dict(workload_config(args.n),
+                       parallelism="independent shards" if world > 1 else "1 GPU",
+                       sample=sample_desc),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
