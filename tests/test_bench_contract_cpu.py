@@ -26,6 +26,10 @@ def test_reference_arm_json_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    # the GPU arm's workload (30M pairs at m=100, E=5), with the timed sample stated
+    cfg = d["config"]
+    assert cfg["n_pairs"] == 30_000_000 and cfg["m"] == 100 and cfg["E"] == 5
+    assert "pairs 0..499" in cfg["sample"]
 
 
 def test_warmup_below_three_is_refused():
