@@ -165,12 +165,16 @@ scan_kernel(const uint32_t *__restrict__ hist, Tables *__restrict__ T)
     for (int k = t; k < kBins; k += 256)
         h[k] = hist[k];
     __syncthreads();
-    {
-        uint32_t p = 0;
-        if (t >= 1)
-            for (int e = 0; e < kMaxE; ++e)
-                p += (h[t * kMaxE + e] + 31u) & ~31u;
-        pad_m[t] = (p + kTile - 1) / kTile * kTile;
+    static_assert(kMaxE == 32, "a lane per threshold");
+    // slots of each m-class: a warp per m, a lane per E (conflict-free reads)
+    const int warp = t >> 5, lane = t & 31;
+    for (int m = warp; m < kMaxM; m += 8) {
+        uint32_t p = m >= 1 ? (h[m * kMaxE + lane] + 31u) & ~31u : 0u;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1)
+            p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (lane == 0)
+            pad_m[m] = (p + kTile - 1) / kTile * kTile;
     }
     __syncthreads();
     if (t == 0) {
@@ -195,12 +199,18 @@ scan_kernel(const uint32_t *__restrict__ hist, Tables *__restrict__ T)
         T->total_slots = slot;
     }
     __syncthreads();
-    if (t >= 1) {
-        uint32_t s = start_m[t];
-        for (int e = 0; e < kMaxE; ++e) {
-            T->bin_slot[t * kMaxE + e] = s;
-            s += (h[t * kMaxE + e] + 31u) & ~31u;
+    // first slot of each bucket (m, E): the m-class start plus the padded sizes
+    // of the buckets of smaller E, by an exclusive scan over the warp's lanes
+    for (int m = 1 + warp; m < kMaxM; m += 8) {
+        const uint32_t v = (h[m * kMaxE + lane] + 31u) & ~31u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o)
+                x += y;
         }
+        T->bin_slot[m * kMaxE + lane] = start_m[m] + x - v;
     }
     __syncthreads();
     if (t < kMaxE) {
