@@ -189,6 +189,24 @@ def warm_until_steady(run, tries: int = 10, tol: float = 0.1):
     return tries
 
 
+def h2d_copy_times(h_reads, h_refs, d_reads, d_refs, chunk, steps):
+    """Wall times (ms) of copying both pinned host row sets to the device in
+    chunks alternating between two streams, as the host pipeline does."""
+    import torch
+    streams = (torch.cuda.Stream(), torch.cuda.Stream())
+    n = h_reads.shape[0]
+    out = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        for k, base in enumerate(range(0, n, chunk)):
+            with torch.cuda.stream(streams[k % 2]):
+                d_reads[base:base + chunk].copy_(h_reads[base:base + chunk], non_blocking=True)
+                d_refs[base:base + chunk].copy_(h_refs[base:base + chunk], non_blocking=True)
+        torch.cuda.synchronize()
+        out.append(round(1000 * (time.perf_counter() - t0), 2))
+    return out
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -774,6 +792,10 @@ def run_ours(args, world, rank, local):
     h_cnt = torch.empty(n, dtype=torch.uint8, pin_memory=True)
     h_idx = torch.empty(n, dtype=torch.int32, pin_memory=True)
     warm_until_steady(lambda: pipe.run(h_reads, h_refs, n, E, h_acc, count=h_cnt, idx=h_idx))
+    # The host link alone: the same input bytes as bare pinned host -> device
+    # copies (chunks on two streams, no kernel), timed like the e2e steps.
+    # Both show the same sporadic stalls on some boxes.
+    copy_ms = h2d_copy_times(h_reads, h_refs, d_reads, d_refs, args.chunk, args.e2e_steps)
     barrier()
     e2e_steps_ms = []
     t0 = time.perf_counter()
@@ -908,6 +930,7 @@ def run_ours(args, world, rank, local):
         "config": dict(workload_config(n), parallelism="independent shards" if world > 1 else "1 GPU"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "step_ms": e2e_steps_ms,
+                "h2d_copy_only_ms": copy_ms,
                 "path": "shouji_pipeline_run, pinned host buffers, chunks of %d pairs" % args.chunk},
         "e2e_packed_input": {
             "value": world * n * args.e2e_steps / e2e_packed_s, "unit": UNIT,
@@ -947,7 +970,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_PAIRS)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=1 << 22)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
