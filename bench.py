@@ -635,7 +635,7 @@ def run_served(args, dev):
 
     drive(64, inflight=16)                       # warm-up: workers of every class are made
     drive(32, inflight=16, resident=True)
-    n_cap = max(16, int(args.serve_seconds * 150))
+    n_cap = max(16, int(args.serve_seconds * 600))   # about a second of closed-loop work
     cap = drive(n_cap, inflight=args.serve_inflight)
     cap_res = drive(n_cap, inflight=args.serve_inflight, resident=True)
     mean_pairs = cap["mean_request_pairs"]
